@@ -1,0 +1,37 @@
+"""CPU oracle for the SP2 density-matrix solver -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, obviously correct FP64 implementations of what the GPU path
+computes, written from the paper (arXiv 2401.13772):
+
+* ``eig.jacobi_eigh`` -- cyclic Jacobi eigendecomposition in plain C (§III,
+  step 1 of the density-matrix procedure).
+* ``sp2.density_projector`` -- D = V f V^T with the zero-temperature
+  occupations (§III, Eq. 2, in the insulating limit the paragraph after it
+  describes): the exact answer SP2 converges to.
+* ``sp2.gershgorin_bounds``, ``sp2.x0_map``, ``sp2.sp2_plain`` -- the SP2
+  recursion of §IV.A step by step (bounds, the shifted/rescaled D_0, the
+  X^2 / 2X - X^2 branches chosen by the trace, idempotency convergence), with
+  numpy's matmul as the only library primitive.
+* ``sp2.spectral_sp2`` -- the same recursion applied to the eigenvalues
+  alone (every iterate is a polynomial in H, so traces, branch choices and the
+  iteration count are fixed by the spectrum).
+* ``mlp`` -- forward/backward of the small MLP used by the learned-sequence
+  path, written as plain numpy algebra, for gradient checks.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package. It shares no code with the CUDA path and the
+CUDA path never imports it.
+"""
+
+from .sp2 import (  # noqa: F401
+    gershgorin_bounds,
+    x0_map,
+    branch_bit,
+    sp2_plain,
+    spectral_sp2,
+    density_projector,
+    invariants,
+    NEARER,
+    PAPER,
+)
+from .eig import jacobi_eigh, build_oracle  # noqa: F401
