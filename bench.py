@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""SP2 density-matrix solves per second on one GB300, through the C ABI.
+
+Workload: the random-cube tight-binding Hamiltonian with 1024 sites x 4
+orbitals (N = 4096, Nocc = 2048, seed 0), the paper-shaped stand-in for the
+dense SP2 benchmarks of arXiv 2401.13772 (§VI). One step = one whole solve:
+Gershgorin bounds, X0 map, the SP2 product loop (decided on the device), and
+the copy of D. Inputs are resident in HBM; L2 is flushed (256 MiB write)
+before every timed step, outside its events.
+
+The JSON line also carries: the end-to-end rate through the same C ABI with
+host buffers (H host->device and D device->host inside the timed region), the
+roofline of the product kernel, the plain FP64 SP2 rate on the same GPU when
+the headline mode is split precision, accuracy invariants of D, clocks
+sampled during the timed region, and the CPU oracle timed on a bounded sample.
+
+--impl reference times the CPU oracle (plain FP64 SP2, numpy) on the host
+cores instead, on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SP2 solves/s & tensor TFLOP/s vs plain FP64 SP2, same GB300, at stated D error"
+UNIT = "solves/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+NOMINAL_BF16_TFLOPS = 2250.0
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64",
+                    choices=["fp64", "fp32_split", "mixed_fp16", "mixed_bf16"])
+    ap.add_argument("--sites", type=int, default=1024)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--fp64-prefix", type=int, default=12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def workload_name(sites, seed):
+    return (f"random-cube tight-binding H, {sites} sites x 4 orbitals (N={4 * sites}), "
+            f"Nocc={2 * sites}, seed {seed}")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.path = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+
+def time_oracle_products(H, nocc, k_sample):
+    """Time the oracle's plain FP64 SP2 (numpy) as it stands: the solve set-up
+    (bounds, X0 map, traces) and k_sample products.
+    Returns (t_setup, t_per_product) in seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.sp2_plain(H, nocc, 0.0, stop_after=0)
+    t1 = time.perf_counter()
+    oracle.sp2_plain(H, nocc, 0.0, stop_after=k_sample)
+    t2 = time.perf_counter()
+    t_setup = t1 - t0
+    return t_setup, max(1e-9, (t2 - t1 - t_setup) / k_sample)
+
+
+def cpu_cores():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+
+def run_reference(args):
+    import numpy as np
+    import oracle
+    from workloads import cube_hamiltonian
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    H, nocc = cube_hamiltonian(args.sites, args.seed)
+    n = H.shape[0]
+    # iteration count of the full solve, from the oracle's spectral SP2 on the
+    # eigenvalues (numpy eigvalsh; not timed) -- only used to scale the sample
+    w = np.linalg.eigvalsh(H)
+    emin, emax = oracle.gershgorin_bounds(H)
+    iters = oracle.spectral_sp2(w, nocc, args.tol, emin, emax)["iters"]
+    k_sample = 2
+    for _ in range(args.warmup):
+        time_oracle_products(H, nocc, 1)
+    times = []
+    for _ in range(args.steps):
+        ts, tp = time_oracle_products(H, nocc, k_sample)
+        times.append(ts + iters * tp)
+    sec = statistics.mean(times)
+    value = 1.0 / sec
+    sample = (f"{k_sample} of {iters} SP2 products (+ bounds and X0) per step on N={n}, "
+              f"scaled to a full solve by the iteration count")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.sites, args.seed), "n": n,
+                       "prec": "fp64 (numpy CPU oracle)", "tol": args.tol},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2401_13772_gb300.build import build
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    import paper_2401_13772_gb300 as pkg
+    from workloads import cube_hamiltonian
+
+    H_np, nocc = cube_hamiltonian(args.sites, args.seed)
+    n = H_np.shape[0]
+    H = torch.from_numpy(H_np).to(dev)
+    D = torch.empty_like(H)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def mk_events(k):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        for e in evs:
+            e.record()
+        return evs
+
+    opts = dict(prec=args.prec, fp64_prefix=args.fp64_prefix)
+    # warm-up (builds the loop graph) and the iteration count
+    info = None
+    for _ in range(max(1, args.warmup)):
+        _, info = pkg.sp2_dense_ex(H, nocc, args.tol, D=D, **opts)
+    iters = info["iters"]
+    body_kernels = 1 if args.prec in ("fp64", "fp32_split") else 2
+    launches_per_solve = 3 + body_kernels * max(iters, 1) + 1
+
+    K = args.steps
+    ev_s, ev_e = mk_events(K), mk_events(K)
+    lp_s, lp_e = mk_events(K), mk_events(K)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    gpu_uuid = None
+    try:
+        gpu_uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not gpu_uuid.startswith("GPU-"):
+            gpu_uuid = "GPU-" + gpu_uuid
+    except Exception:
+        gpu_uuid = None
+    clocks = ClockSampler(gpu_uuid)
+    clocks.start()
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.zero_()
+        ev_s[i].record(stream)
+        pkg.sp2_dense_ex(H, nocc, args.tol, D=D, info=False, loop_events=(lp_s[i], lp_e[i]),
+                         **opts)
+        ev_e[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [ev_s[i].elapsed_time(ev_e[i]) for i in range(K)]
+    loop_ms = [lp_s[i].elapsed_time(lp_e[i]) for i in range(K)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * K / (total_ms / 1e3)
+    ms_per_step = total_ms / K
+
+    # per-solve check of the result (status of the last timed solve)
+    _, qinfo = pkg.sp2_dense_ex(H, nocc, args.tol, D=D, **opts)
+    # accuracy invariants of D (torch FP64 matmul, outside the timed region)
+    Dd = D
+    idem = float((Dd @ Dd - Dd).abs().max())
+    trace_err = abs(float(torch.trace(Dd)) - nocc)
+    comm = float((H @ Dd - Dd @ H).abs().max()) / float(H.abs().max())
+
+    # dominant kernel: the product step, timed as loop time / products
+    flops_alg = float(n) * n * (n + 1)  # one symmetric square, upper triangle
+    step_kernel_ms = statistics.mean(loop_ms) / max(iters, 1)
+    peaks, peak_src = load_peaks()
+    if args.prec == "fp64":
+        peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]) * (
+            NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS)
+        peak_note = f"fp64: {peak_src} bf16 burst x nominal fp64/bf16 ratio (1.25/2250)"
+    else:
+        peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
+        peak_note = f"fp16/bf16 dense, {peak_src} burst"
+    achieved = flops_alg / (step_kernel_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "square_fp64_kernel" if args.prec == "fp64" else "square_split_kernel",
+                "peak_source": peak_note,
+                "flops_per_launch": flops_alg, "avg_launch_ms": step_kernel_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32_split": "f16x2 split, f32 accumulate, f64 traces",
+                      "mixed_fp16": "f64 prefix/refine + f16x2 split",
+                      "mixed_bf16": "f64 prefix/refine + bf16x3 split"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.sites, args.seed), "n": n, "nocc": nocc,
+                       "prec": args.prec, "tol": args.tol, "rule": "nearer",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "flushed before each step (256 MiB write, outside events)"},
+            "iters": iters, "status": qinfo["status"], "phase_iters": qinfo["phase_iters"],
+            "tflops_algorithmic": iters * flops_alg / (ms_per_step * 1e-3) / 1e12,
+            "d_check": {"idempotency_max": idem, "trace_err": trace_err,
+                        "commutator_max_rel": comm},
+            "roofline": roofline, "gpu_launches": launches_per_solve * K,
+            "clocks": clk}
+
+    # end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        Hh = torch.from_numpy(H_np).pin_memory()
+        Dh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        Hd2 = torch.empty_like(H)
+        Dd2 = torch.empty_like(H)
+        es, ee = mk_events(K), mk_events(K)
+        torch.cuda.synchronize()
+        for i in range(K):
+            flush.zero_()
+            es[i].record(stream)
+            Hd2.copy_(Hh, non_blocking=True)
+            pkg.sp2_dense(Hd2, nocc, args.tol, D=Dd2) if args.prec == "fp64" else \
+                pkg.sp2_dense_ex(Hd2, nocc, args.tol, D=Dd2, info=False, **opts)
+            Dh.copy_(Dd2, non_blocking=True)
+            ee[i].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = sum(es[i].elapsed_time(ee[i]) for i in range(K))
+        if world > 1:
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        line["e2e"] = {"value": world * K / (e2e_ms / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8}
+
+    # plain FP64 SP2 on the same GPU (the comparison the metric asks for)
+    if args.prec != "fp64" and not args.no_fp64_baseline:
+        _, i64 = pkg.sp2_dense_ex(H, nocc, args.tol, D=D, prec="fp64")
+        e0, e1 = mk_events(1)[0], mk_events(1)[0]
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0.record(stream)
+        pkg.sp2_dense_ex(H, nocc, args.tol, D=D, info=False, prec="fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        line["fp64_baseline"] = {"value": 1e3 / t64, "unit": UNIT, "iters": i64["iters"],
+                                 "speedup": (value / world) / (1e3 / t64)}
+
+    # CPU oracle on the host cores (rank 0, N = 1 only), bounded sample
+    if world == 1 and not args.no_cpu_baseline:
+        k_sample = 2
+        ts, tp = time_oracle_products(H_np, nocc, k_sample)
+        sec = ts + iters * tp
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": cpu_cores(),
+                                "kind": "oracle",
+                                "sample": f"{k_sample} of {iters} SP2 products (+ bounds and X0) "
+                                          f"of the same N={n} solve, numpy FP64 matmul, scaled "
+                                          f"to a full solve by the iteration count"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

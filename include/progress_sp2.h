@@ -1,0 +1,155 @@
+/*
+ * progress_sp2.h -- C ABI of the GB300 (sm_103a) SP2 density-matrix solver.
+ *
+ * The operation (arXiv 2401.13772):
+ *   §III   D = V f V^T, the zero-temperature density matrix of a symmetric H
+ *          with Nocc occupied states (the insulating limit: f = 1 below the
+ *          gap, 0 above).
+ *   §IV.A  SP2 reaches that D with matrix products only: X0 = (emax I - H) /
+ *          (emax - emin), then X <- X^2 when the trace is above Nocc and
+ *          X <- 2X - X^2 when it is below, until X is idempotent (Listing 1,
+ *          prg_sp2, gives the loop).
+ *   §VIII.A  emin, emax come from Gershgorin circles.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are dense, real, FP64, square n x n, row-major with leading
+ *     dimension n. H and D are symmetric, so row-major equals column-major.
+ *   - All matrix pointers are DEVICE pointers owned by the caller, except where
+ *     a comment says host. The library never frees caller memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Every call is
+ *     asynchronous on that stream unless its comment says it synchronizes.
+ *   - Work buffers (ping-pong iterates, operand slices, partial traces) are
+ *     allocated by the library on first use per (device, stream) and cached;
+ *     progress_release() frees them. Calls on one stream are serialized by the
+ *     stream; concurrent calls on different streams use different workspaces.
+ *   - Nothing aborts. Each call returns a progress_status_t; argument errors
+ *     are reported before any work is queued. A failed CUDA call returns
+ *     PROGRESS_ECUDA and progress_last_error() describes it.
+ *   - The GPU decides each SP2 branch and the stopping point itself: no host
+ *     round trip per iteration (the paper's listing reads the trace on the host
+ *     every iteration).
+ */
+#ifndef PROGRESS_SP2_H
+#define PROGRESS_SP2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PROGRESS_OK = 0,
+  PROGRESS_EINVAL = 1,      /* bad argument (sizes, nocc outside [0, n], NULL pointer) */
+  PROGRESS_ENOCONV = 2,     /* maxiter products without reaching tol; D holds the last iterate */
+  PROGRESS_EBOUNDS = 3,     /* the iterate left [0, 1] (bounds do not enclose the spectrum) or is not finite */
+  PROGRESS_ECUDA = 4,       /* a CUDA runtime call failed */
+  PROGRESS_ENOMEM = 5,      /* device workspace allocation failed */
+  PROGRESS_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+  PROGRESS_EUNSUPPORTED = 7 /* the requested mode is not available on this device */
+} progress_status_t;
+
+/* Arithmetic of the squarings X*X. Traces, branch decisions, the convergence
+ * test and the bounds are FP64 in every mode. */
+typedef enum {
+  PROGRESS_FP64 = 0,        /* every product in FP64 */
+  PROGRESS_FP32_SPLIT = 1,  /* every product as fp16 hi+lo operand splits on tcgen05 tensor
+                               cores with FP32 accumulation (~FP32 accuracy) */
+  PROGRESS_MIXED_FP16 = 2,  /* fp64_prefix FP64 products, then fp16 hi+lo split products, then
+                               FP64 refinement products until idempotent in FP64 */
+  PROGRESS_MIXED_BF16 = 3   /* as MIXED_FP16 with bf16 hi+mid+lo (3-way) splits */
+} progress_prec_t;
+
+typedef enum {
+  PROGRESS_RULE_NEARER = 0, /* take the branch whose trace lands nearer Nocc; needs no extra
+                               work because Tr X^2 = ||X||_F^2 is known before the product */
+  PROGRESS_RULE_PAPER = 1   /* 2X - X^2 iff Tr X - Nocc <= 0 (Listing 1's test) */
+} progress_rule_t;
+
+typedef struct {
+  int32_t prec;         /* progress_prec_t */
+  int32_t rule;         /* progress_rule_t */
+  int32_t fp64_prefix;  /* MIXED_*: FP64 products before the split phase (default 12) */
+  int32_t maxiter;      /* cap on products (default 100, at most 250) */
+  double emin, emax;    /* spectral bounds; NaN (default) = Gershgorin estimate */
+  int32_t loop_mode;    /* 0 = CUDA graph with a device-side WHILE node (default),
+                           1 = maxiter plain launches that exit early once done */
+  int32_t reserved0;    /* must be zero */
+  void* loop_events[2]; /* optional cudaEvent_t pair (or NULL) recorded on the stream
+                           right before and right after the product loop, so a
+                           caller can time the products alone */
+  int32_t reserved[4];  /* must be zero */
+} progress_opts_t;
+
+/* Result of one solve, read back from the device by the calls that take it. */
+typedef struct {
+  int32_t status;        /* progress_status_t of the solve */
+  int32_t iters;         /* products performed */
+  int32_t converged;     /* 1 if |Tr X^2 - Tr X| < tol was reached */
+  int32_t phase_iters[3];/* products in FP64 prefix / split phase / FP64 refinement */
+  double emin, emax;     /* bounds used */
+  double trace;          /* Tr D */
+  double idempotency;    /* |Tr D^2 - Tr D| of the returned D */
+  uint64_t bits[4];      /* branch of product k is bit (k % 64) of bits[k / 64]; 1 = 2X - X^2 */
+} progress_info_t;
+
+/* Fill *opts with the defaults listed above. */
+void progress_opts_default(progress_opts_t* opts);
+
+/*
+ * Gershgorin enclosure of the spectrum of the symmetric H (§VIII.A; the emin,
+ * emax that Listing 1 uses): R_i = sum_{j != i} |H_ij|,
+ * d_bounds[0] = min_i (H_ii - R_i), d_bounds[1] = max_i (H_ii + R_i).
+ *   dH        device, n x n FP64 row-major, read only
+ *   d_bounds  device, 2 doubles, written
+ * Errors: EINVAL if n < 1 or a pointer is NULL.
+ */
+progress_status_t progress_gershgorin_bounds(const double* dH, int64_t n, double* d_bounds,
+                                             void* stream);
+
+/*
+ * SP2 density matrix with default options (FP64 products, nearer rule,
+ * Gershgorin bounds, maxiter 100). Asynchronous: the convergence status of
+ * the solve is available from progress_sp2_query().
+ *   dH    device, n x n FP64, read only (H is never written)
+ *   n     matrix order, >= 0 (n = 0 is a no-op)
+ *   nocc  occupied states (spin factor excluded), 0 <= nocc <= n
+ *   tol   stop once |Tr X^2 - Tr X| < tol (tol >= 0)
+ *   dD    device, n x n FP64, written; must not overlap dH
+ * Errors: EINVAL for bad sizes/pointers; ENOMEM; ECUDA.
+ */
+progress_status_t progress_sp2_dense(const double* dH, int64_t n, int64_t nocc, double tol,
+                                     double* dD, void* stream);
+
+/*
+ * SP2 with options. If info is not NULL the call synchronizes the stream,
+ * fills *info (host memory) and returns the solve's status (ENOCONV, EBOUNDS
+ * ...); otherwise it is asynchronous like progress_sp2_dense. opts may be NULL
+ * (defaults). dD may equal dH (in place) in this entry point only.
+ * Errors: as progress_sp2_dense, plus EUNSUPPORTED when a split-precision mode
+ * is asked on a device without tcgen05 tensor cores (sm_100 family).
+ */
+progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t nocc, double tol,
+                                        double* dD, const progress_opts_t* opts,
+                                        progress_info_t* info, void* stream);
+
+/* Synchronize `stream` and report the last solve queued on it. */
+progress_status_t progress_sp2_query(void* stream, progress_info_t* info);
+
+/* Free the cached workspace of `stream` on the current device (synchronizes it). */
+progress_status_t progress_release(void* stream);
+
+/* Free every cached workspace of the current device (synchronizes the device). */
+progress_status_t progress_release_all(void);
+
+/* Text of the last error recorded by this thread (never NULL). */
+const char* progress_last_error(void);
+
+/* Library version, e.g. "0.1.0". */
+const char* progress_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROGRESS_SP2_H */

@@ -20,6 +20,8 @@ Readings where the paper is silent (each also listed in the design notes):
   Tr(X^2) = t2, Tr(2X - X^2) = 2 t1 - t2. Take 2X - X^2 iff
   |t2 - Nocc| - |2 t1 - t2 - Nocc| > 1e-12 * n; a tie takes X^2.
 * Branch rule PAPER: 2X - X^2 iff t1 - Nocc <= 0 (the listing's test).
+* A zero-width Gershgorin interval (H = c I, n = 1) is widened by 1 on each
+  side before the X0 map.
 * Convergence ("check for convergence", elided in the listing): stop before
   the next product once |Tr X^2 - Tr X| = |t2 - t1| < tol. The iteration count
   is the number of products performed.
@@ -74,6 +76,10 @@ def sp2_plain(H, nocc, tol, rule=NEARER, maxiter=100, bounds=None, stop_after=No
     H = np.asarray(H, dtype=np.float64)
     n = H.shape[0]
     emin, emax = gershgorin_bounds(H) if bounds is None else bounds
+    if not emax > emin:
+        # zero-width enclosure (H = c I, n = 1): widen by 1 on each side so the
+        # X0 map is defined and the spectrum is still enclosed
+        emin, emax = emin - 1.0, emax + 1.0
     X = x0_map(H, emin, emax)
     bits, t1s, t2s = [], [], []
     converged = False

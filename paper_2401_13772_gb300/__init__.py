@@ -1,0 +1,123 @@
+"""GB300 (sm_103a) SP2 density-matrix solver: Python binding of the C ABI.
+
+The solver computes the zero-temperature density matrix D of a real symmetric
+Hamiltonian H with the SP2 recursive purification of arXiv 2401.13772 §IV.A:
+Gershgorin bounds (§VIII.A), X0 = (emax I - H)/(emax - emin), then
+X <- X^2 or 2X - X^2 chosen by the trace until X is idempotent.
+
+Every function here only marshals torch CUDA tensors (device memory and the
+current stream) into the C ABI declared in include/progress_sp2.h; all
+arithmetic runs in the library's CUDA kernels. There is no CPU fallback: the
+calls raise when the library is missing or the tensors are not on a GPU.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16, RULE_NEARER, RULE_PAPER,
+    Info, Opts, ProgressError, load, check,
+)
+
+__all__ = ["gershgorin_bounds", "sp2_dense", "sp2_dense_ex", "release", "load",
+           "FP64", "FP32_SPLIT", "MIXED_FP16", "MIXED_BF16", "RULE_NEARER", "RULE_PAPER",
+           "PREC_NAMES", "ProgressError"]
+
+PREC_NAMES = {"fp64": FP64, "fp32_split": FP32_SPLIT, "mixed_fp16": MIXED_FP16,
+              "mixed_bf16": MIXED_BF16}
+RULE_NAMES = {"nearer": RULE_NEARER, "paper": RULE_PAPER}
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_matrix(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if t.dim() != 2 or t.shape[0] != t.shape[1]:
+        raise ValueError(f"{name} must be square")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (row-major)")
+
+
+def gershgorin_bounds(H, out=None, stream=None):
+    """Device tensor [emin, emax] of Gershgorin bounds of H (§VIII.A)."""
+    import torch
+    _check_matrix(H, "H")
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=H.device)
+    with torch.cuda.device(H.device):
+        check(load().progress_gershgorin_bounds(ctypes.c_void_p(H.data_ptr()), H.shape[0],
+                                                ctypes.c_void_p(out.data_ptr()),
+                                                _stream_ptr(stream)))
+    return out
+
+
+def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None, emax=None,
+              loop_mode=0, loop_events=None):
+    o = Opts()
+    load().progress_opts_default(ctypes.byref(o))
+    o.prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
+    o.rule = RULE_NAMES[rule] if isinstance(rule, str) else int(rule)
+    o.fp64_prefix = int(fp64_prefix)
+    o.maxiter = int(maxiter)
+    o.emin = math.nan if emin is None else float(emin)
+    o.emax = math.nan if emax is None else float(emax)
+    o.loop_mode = int(loop_mode)
+    if loop_events is not None:
+        # torch.cuda.Event pair, already created (recorded once)
+        o.loop_events[0] = loop_events[0].cuda_event
+        o.loop_events[1] = loop_events[1].cuda_event
+    return o
+
+
+def sp2_dense(H, nocc, tol, D=None, stream=None):
+    """Asynchronous FP64 SP2 solve with default options; returns D."""
+    import torch
+    _check_matrix(H, "H")
+    if D is None:
+        D = torch.empty_like(H)
+    _check_matrix(D, "D")
+    with torch.cuda.device(H.device):
+        check(load().progress_sp2_dense(ctypes.c_void_p(H.data_ptr()), H.shape[0], int(nocc),
+                                        float(tol), ctypes.c_void_p(D.data_ptr()),
+                                        _stream_ptr(stream)))
+    return D
+
+
+def sp2_dense_ex(H, nocc, tol, D=None, info=True, stream=None, raise_on_status=True, **opts):
+    """SP2 solve with options (prec, rule, fp64_prefix, maxiter, emin, emax,
+    loop_mode, loop_events). With info=True it synchronizes and returns
+    (D, info dict)."""
+    import torch
+    _check_matrix(H, "H")
+    if D is None:
+        D = torch.empty_like(H)
+    _check_matrix(D, "D")
+    o = make_opts(**opts)
+    inf = _lib.Info() if info else None
+    with torch.cuda.device(H.device):
+        st = load().progress_sp2_dense_ex(ctypes.c_void_p(H.data_ptr()), H.shape[0], int(nocc),
+                                          float(tol), ctypes.c_void_p(D.data_ptr()),
+                                          ctypes.byref(o),
+                                          ctypes.byref(inf) if info else None,
+                                          _stream_ptr(stream))
+    if st != _lib.OK and (raise_on_status or st not in (_lib.ENOCONV, _lib.EBOUNDS)):
+        check(st)
+    if info:
+        return D, inf.to_dict()
+    return D
+
+
+def release(stream=None):
+    """Free the library's cached workspace of the stream."""
+    check(load().progress_release(_stream_ptr(stream)))

@@ -1,0 +1,101 @@
+"""ctypes declarations of the C ABI in include/progress_sp2.h.
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+Loading fails loudly when the library has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB_PATH
+
+OK, EINVAL, ENOCONV, EBOUNDS, ECUDA, ENOMEM, ETIMEOUT, EUNSUPPORTED = range(8)
+STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOCONV: "ENOCONV", EBOUNDS: "EBOUNDS",
+                ECUDA: "ECUDA", ENOMEM: "ENOMEM", ETIMEOUT: "ETIMEOUT",
+                EUNSUPPORTED: "EUNSUPPORTED"}
+
+FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16 = range(4)
+RULE_NEARER, RULE_PAPER = 0, 1
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("rule", ctypes.c_int32),
+                ("fp64_prefix", ctypes.c_int32), ("maxiter", ctypes.c_int32),
+                ("emin", ctypes.c_double), ("emax", ctypes.c_double),
+                ("loop_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("loop_events", ctypes.c_void_p * 2), ("reserved", ctypes.c_int32 * 4)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("phase_iters", ctypes.c_int32 * 3),
+                ("emin", ctypes.c_double), ("emax", ctypes.c_double),
+                ("trace", ctypes.c_double), ("idempotency", ctypes.c_double),
+                ("bits", ctypes.c_uint64 * 4)]
+
+    def to_dict(self):
+        bits = [(self.bits[k // 64] >> (k % 64)) & 1 for k in range(self.iters)]
+        return {"status": STATUS_NAMES.get(self.status, str(self.status)),
+                "iters": self.iters, "converged": bool(self.converged),
+                "phase_iters": list(self.phase_iters), "emin": self.emin,
+                "emax": self.emax, "trace": self.trace,
+                "idempotency": self.idempotency, "bits": bits}
+
+
+# symbol -> (restype, argtypes); every function declared in include/progress_sp2.h
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+SIGNATURES = {
+    "progress_opts_default": (None, [ctypes.POINTER(Opts)]),
+    "progress_gershgorin_bounds": (ctypes.c_int, [_P, _I64, _P, _P]),
+    "progress_sp2_dense": (ctypes.c_int, [_P, _I64, _I64, _D, _P, _P]),
+    "progress_sp2_dense_ex": (ctypes.c_int, [_P, _I64, _I64, _D, _P, ctypes.POINTER(Opts),
+                                             ctypes.POINTER(Info), _P]),
+    "progress_sp2_query": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "progress_release": (ctypes.c_int, [_P]),
+    "progress_release_all": (ctypes.c_int, []),
+    "progress_last_error": (ctypes.c_char_p, []),
+    "progress_version": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ProgressError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return os.environ.get("PROGRESS_SP2_LIB", LIB_PATH)
+
+
+def load():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: run "
+                               "paper_2401_13772_gb300.build.build() (needs nvcc)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def check(status: int):
+    if status != OK:
+        msg = load().progress_last_error().decode(errors="replace")
+        raise ProgressError(status, msg)

@@ -1,0 +1,419 @@
+// C ABI of the SP2 solver: argument checks, per-(device, stream) workspace
+// cache, the device-driven iteration loop (a CUDA graph with a WHILE node)
+// and readback of the solve state.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include "progress_sp2.h"
+#include "sp2_common.cuh"
+#include "sp2_launch.h"
+#include "sp2_slices.cuh"
+
+namespace {
+
+thread_local std::string g_err = "";
+
+progress_status_t fail(progress_status_t s, const char* what) {
+  g_err = what;
+  return s;
+}
+
+progress_status_t cuda_fail(cudaError_t e, const char* where) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+  g_err = buf;
+  cudaGetLastError();  // clear a sticky-free error so later calls start clean
+  return e == cudaErrorMemoryAllocation ? PROGRESS_ENOMEM : PROGRESS_ECUDA;
+}
+
+#define CK(call, where)                              \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+struct Workspace {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  int ld_cap = 0;       // ld the matrix buffers were sized for
+  int x64_cap = 0;      // ld of the FP64 ping-pong buffers (0 = none)
+  int slices_cap = 0;   // slices per set that are allocated
+  sp2::DevBuffers buf{};
+  sp2::State* h_state = nullptr;  // pinned host mirror for readback
+  cudaStream_t cap_stream = nullptr;
+  // cached loop graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int g_ld = -1, g_prec = -1, g_fmt = -1;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace*> g_ws;
+
+void free_graph(Workspace* w) {
+  if (w->exec) cudaGraphExecDestroy(w->exec);
+  if (w->graph) cudaGraphDestroy(w->graph);
+  w->exec = nullptr;
+  w->graph = nullptr;
+  w->g_ld = w->g_prec = w->g_fmt = -1;
+}
+
+void free_matrices(Workspace* w) {
+  for (int k = 0; k < 2; ++k) {
+    if (w->buf.x64[k]) cudaFree(w->buf.x64[k]);
+    w->buf.x64[k] = nullptr;
+    for (int i = 0; i < 3; ++i) {
+      if (w->buf.sl[k][i]) cudaFree(w->buf.sl[k][i]);
+      w->buf.sl[k][i] = nullptr;
+    }
+  }
+  if (w->buf.partials) cudaFree(w->buf.partials);
+  w->buf.partials = nullptr;
+  w->buf.max_partials = 0;
+  w->x64_cap = w->slices_cap = w->ld_cap = 0;
+}
+
+void free_workspace(Workspace* w) {
+  free_graph(w);
+  free_matrices(w);
+  if (w->buf.st) cudaFree(w->buf.st);
+  if (w->h_state) cudaFreeHost(w->h_state);
+  if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
+  delete w;
+}
+
+progress_status_t get_workspace(cudaStream_t s, Workspace** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto key = std::make_pair(dev, s);
+  auto it = g_ws.find(key);
+  if (it != g_ws.end()) {
+    *out = it->second;
+    return PROGRESS_OK;
+  }
+  Workspace* w = new Workspace();
+  w->device = dev;
+  w->stream = s;
+  cudaError_t e = cudaMalloc(&w->buf.st, sizeof(sp2::State));
+  if (e == cudaSuccess) e = cudaMallocHost(&w->h_state, sizeof(sp2::State));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemset(w->buf.st, 0, sizeof(sp2::State));
+  if (e != cudaSuccess) {
+    free_workspace(w);
+    return cuda_fail(e, "workspace allocation");
+  }
+  g_ws[key] = w;
+  *out = w;
+  return PROGRESS_OK;
+}
+
+// Make sure the matrix buffers cover ld and the requested formats.
+progress_status_t ensure_buffers(Workspace* w, int ld, bool need_x64, int nslices) {
+  const bool grow = ld > w->ld_cap || (need_x64 && w->x64_cap < ld) ||
+                    (nslices > 0 && (w->slices_cap < nslices || w->ld_cap < ld));
+  if (!grow && w->buf.partials) return PROGRESS_OK;
+  CK(cudaStreamSynchronize(w->stream), "cudaStreamSynchronize");
+  const int new_ld = ld > w->ld_cap ? ld : w->ld_cap;
+  const bool keep_x64 = w->x64_cap > 0;
+  const int keep_sl = w->slices_cap;
+  free_graph(w);
+  free_matrices(w);
+  const size_t elems = (size_t)new_ld * new_ld;
+  const bool x64 = need_x64 || keep_x64;
+  const int ns = nslices > keep_sl ? nslices : keep_sl;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    if (x64) e = cudaMalloc(&w->buf.x64[k], elems * sizeof(double));
+    for (int i = 0; i < ns && e == cudaSuccess; ++i)
+      e = cudaMalloc(&w->buf.sl[k][i], elems * sizeof(uint16_t));
+  }
+  int maxp = sp2::fp64_tile_count(new_ld);
+  const int sp = sp2::split_tile_count(new_ld);
+  if (sp > maxp) maxp = sp;
+  if (maxp < 152 * 8) maxp = 152 * 8;
+  if (e == cudaSuccess) e = cudaMalloc(&w->buf.partials, (size_t)maxp * 2 * sizeof(double));
+  if (e != cudaSuccess) {
+    free_matrices(w);
+    return cuda_fail(e, "workspace matrix allocation");
+  }
+  w->buf.max_partials = maxp;
+  w->ld_cap = new_ld;
+  w->x64_cap = x64 ? new_ld : 0;
+  w->slices_cap = ns;
+  return PROGRESS_OK;
+}
+
+bool is_mixed(int prec) { return prec == PROGRESS_MIXED_FP16 || prec == PROGRESS_MIXED_BF16; }
+
+int slice_fmt_of(int prec) {
+  return prec == PROGRESS_MIXED_BF16 ? sp2::kBF16x3 : sp2::kFP16x2;
+}
+
+// Queue the product steps of one loop iteration on `s`.
+progress_status_t queue_steps(Workspace* w, const sp2::SolveParams& p, unsigned long long cond,
+                              cudaStream_t s) {
+  if (p.prec == PROGRESS_FP64 || is_mixed(p.prec))
+    CK(sp2::launch_square_fp64(w->buf, p.ld, p.slice_fmt, cond, s), "square_fp64 launch");
+  if (p.prec != PROGRESS_FP64)
+    CK(sp2::launch_square_split(w->buf, p, cond, s), "square_split launch");
+  return PROGRESS_OK;
+}
+
+progress_status_t build_graph(Workspace* w, const sp2::SolveParams& p) {
+  if (w->exec && w->g_ld == p.ld && w->g_prec == p.prec && w->g_fmt == p.slice_fmt)
+    return PROGRESS_OK;
+  free_graph(w);
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphConditionalHandleCreate");
+  }
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphAddNode(conditional)");
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(w->cap_stream, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+  }
+  progress_status_t qs = queue_steps(w, p, (unsigned long long)h, w->cap_stream);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(w->cap_stream, &captured);
+  if (qs != PROGRESS_OK || e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return qs != PROGRESS_OK ? qs : cuda_fail(e, "cudaStreamEndCapture");
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  w->graph = g;
+  w->exec = exec;
+  w->g_ld = p.ld;
+  w->g_prec = p.prec;
+  w->g_fmt = p.slice_fmt;
+  return PROGRESS_OK;
+}
+
+int round_up(int64_t n, int m) { return (int)((n + m - 1) / m * m); }
+
+void fill_info(const sp2::State& s, progress_info_t* info) {
+  memset(info, 0, sizeof *info);
+  info->status = s.status;
+  info->iters = s.iter;
+  info->converged = s.converged;
+  for (int i = 0; i < 3; ++i) info->phase_iters[i] = s.phase_iters[i];
+  info->emin = s.emin;
+  info->emax = s.emax;
+  info->trace = s.t1;
+  info->idempotency = s.idem;
+  for (int i = 0; i < 4; ++i) info->bits[i] = s.bits[i];
+}
+
+progress_status_t query(Workspace* w, progress_info_t* info) {
+  CK(cudaMemcpyAsync(w->h_state, w->buf.st, sizeof(sp2::State), cudaMemcpyDeviceToHost,
+                     w->stream),
+     "state readback");
+  CK(cudaStreamSynchronize(w->stream), "cudaStreamSynchronize");
+  fill_info(*w->h_state, info);
+  if (w->h_state->status != PROGRESS_OK) {
+    g_err = w->h_state->status == PROGRESS_ENOCONV ? "SP2 did not converge within maxiter"
+                                                   : "SP2 iterate left [0,1] (bad bounds or input)";
+    return (progress_status_t)w->h_state->status;
+  }
+  return PROGRESS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void progress_opts_default(progress_opts_t* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->prec = PROGRESS_FP64;
+  o->rule = PROGRESS_RULE_NEARER;
+  o->fp64_prefix = 12;
+  o->maxiter = 100;
+  o->emin = NAN;
+  o->emax = NAN;
+  o->loop_mode = 0;
+}
+
+const char* progress_last_error(void) { return g_err.c_str(); }
+
+const char* progress_version(void) { return "0.1.0"; }
+
+progress_status_t progress_gershgorin_bounds(const double* dH, int64_t n, double* d_bounds,
+                                             void* stream) {
+  if (n < 1 || !dH || !d_bounds) return fail(PROGRESS_EINVAL, "gershgorin: n < 1 or NULL pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = nullptr;
+  progress_status_t st = get_workspace(s, &w);
+  if (st != PROGRESS_OK) return st;
+  if (!w->buf.partials) {
+    st = ensure_buffers(w, 128, false, 0);
+    if (st != PROGRESS_OK) return st;
+  }
+  sp2::SolveParams p;
+  memset(&p, 0, sizeof p);
+  p.n = n;
+  p.ld = 0;
+  p.emin_override = NAN;
+  p.emax_override = NAN;
+  CK(sp2::launch_init(w->buf, p, s), "init launch");
+  CK(sp2::launch_gershgorin(dH, n, w->buf, d_bounds, s), "gershgorin launch");
+  return PROGRESS_OK;
+}
+
+progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t nocc, double tol,
+                                        double* dD, const progress_opts_t* opts,
+                                        progress_info_t* info, void* stream) {
+  progress_opts_t o;
+  if (opts) {
+    o = *opts;
+  } else {
+    progress_opts_default(&o);
+  }
+  if (n < 0 || n > (1 << 16)) return fail(PROGRESS_EINVAL, "n must be in [0, 65536]");
+  if (nocc < 0 || nocc > n) return fail(PROGRESS_EINVAL, "nocc must be in [0, n]");
+  if (!(tol >= 0.0)) return fail(PROGRESS_EINVAL, "tol must be >= 0");
+  if (o.prec < PROGRESS_FP64 || o.prec > PROGRESS_MIXED_BF16)
+    return fail(PROGRESS_EINVAL, "unknown precision mode");
+  if (o.rule != PROGRESS_RULE_NEARER && o.rule != PROGRESS_RULE_PAPER)
+    return fail(PROGRESS_EINVAL, "unknown branch rule");
+  if (o.maxiter < 0 || o.maxiter > sp2::kMaxHist - 6)
+    return fail(PROGRESS_EINVAL, "maxiter must be in [0, 250]");
+  if (o.fp64_prefix < 0) return fail(PROGRESS_EINVAL, "fp64_prefix must be >= 0");
+  if (o.loop_mode != 0 && o.loop_mode != 1) return fail(PROGRESS_EINVAL, "loop_mode must be 0 or 1");
+  if (!isnan(o.emin) || !isnan(o.emax)) {
+    if (isnan(o.emin) || isnan(o.emax) || !(o.emax > o.emin))
+      return fail(PROGRESS_EINVAL, "bounds override needs emin < emax (both set)");
+  }
+  if (n == 0) {
+    if (info) memset(info, 0, sizeof *info);
+    if (info) info->converged = 1;
+    return PROGRESS_OK;
+  }
+  if (!dH || !dD) return fail(PROGRESS_EINVAL, "NULL matrix pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (o.prec != PROGRESS_FP64) {
+    int dev = 0, major = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev),
+       "cudaDeviceGetAttribute");
+    if (major != 10) return fail(PROGRESS_EUNSUPPORTED, "split precision needs an sm_10x GPU");
+  }
+  Workspace* w = nullptr;
+  progress_status_t st = get_workspace(s, &w);
+  if (st != PROGRESS_OK) return st;
+  const int ld = round_up(n, 128);
+  const bool need_x64 = o.prec != PROGRESS_FP32_SPLIT;
+  const int fmt = slice_fmt_of(o.prec);
+  const int nslices = o.prec == PROGRESS_FP64 ? 0 : (fmt == sp2::kBF16x3 ? 3 : 2);
+  st = ensure_buffers(w, ld, need_x64, nslices);
+  if (st != PROGRESS_OK) return st;
+
+  sp2::SolveParams p;
+  memset(&p, 0, sizeof p);
+  p.n = n;
+  p.ld = ld;
+  p.nocc = nocc;
+  p.rule = o.rule;
+  p.maxiter = o.maxiter;
+  p.prec = o.prec;
+  p.fp64_prefix = o.fp64_prefix;
+  p.slice_fmt = fmt;
+  p.tol = tol;
+  p.emin_override = o.emin;
+  p.emax_override = o.emax;
+
+  CK(sp2::launch_init(w->buf, p, s), "init launch");
+  CK(sp2::launch_gershgorin(dH, n, w->buf, nullptr, s), "gershgorin launch");
+  CK(sp2::launch_x0(dH, w->buf, p, s), "x0 launch");
+  if (o.loop_events[0]) CK(cudaEventRecord((cudaEvent_t)o.loop_events[0], s), "event record");
+  if (o.loop_mode == 0) {
+    st = build_graph(w, p);
+    if (st != PROGRESS_OK) return st;
+    CK(cudaGraphLaunch(w->exec, s), "cudaGraphLaunch");
+  } else {
+    for (int i = 0; i < o.maxiter + 1; ++i) {
+      st = queue_steps(w, p, 0ull, s);
+      if (st != PROGRESS_OK) return st;
+    }
+  }
+  if (o.loop_events[1]) CK(cudaEventRecord((cudaEvent_t)o.loop_events[1], s), "event record");
+  CK(sp2::launch_finalize(w->buf, dD, n, ld, fmt, s), "finalize launch");
+  if (info) return query(w, info);
+  return PROGRESS_OK;
+}
+
+progress_status_t progress_sp2_dense(const double* dH, int64_t n, int64_t nocc, double tol,
+                                     double* dD, void* stream) {
+  if (n > 0 && dH == dD) return fail(PROGRESS_EINVAL, "dD must not overlap dH");
+  return progress_sp2_dense_ex(dH, n, nocc, tol, dD, nullptr, nullptr, stream);
+}
+
+progress_status_t progress_sp2_query(void* stream, progress_info_t* info) {
+  if (!info) return fail(PROGRESS_EINVAL, "info is NULL");
+  Workspace* w = nullptr;
+  progress_status_t st = get_workspace((cudaStream_t)stream, &w);
+  if (st != PROGRESS_OK) return st;
+  return query(w, info);
+}
+
+progress_status_t progress_release(void* stream) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  Workspace* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_ws.find(std::make_pair(dev, (cudaStream_t)stream));
+    if (it == g_ws.end()) return PROGRESS_OK;
+    w = it->second;
+    g_ws.erase(it);
+  }
+  CK(cudaStreamSynchronize(w->stream), "cudaStreamSynchronize");
+  free_workspace(w);
+  return PROGRESS_OK;
+}
+
+progress_status_t progress_release_all(void) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto it = g_ws.begin(); it != g_ws.end();) {
+    if (it->first.first == dev) {
+      free_workspace(it->second);
+      it = g_ws.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return PROGRESS_OK;
+}
+
+}  // extern "C"

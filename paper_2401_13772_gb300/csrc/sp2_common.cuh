@@ -1,0 +1,210 @@
+// Shared device-side state and helpers of the SP2 solver kernels.
+//
+// The SP2 loop (§IV.A) keeps its whole control state on the device: the
+// traces of the current iterate, the branch of the next product, the
+// iteration count and the stop flag. Every product kernel's last CTA reduces
+// the per-tile partial traces in a fixed order (deterministic), then decides
+// the next step, so the host never reads a trace inside the loop.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "progress_sp2.h"
+
+namespace sp2 {
+
+constexpr int kMaxHist = 256;  // branch/idempotency history length (maxiter <= 250)
+
+// Precision of one product.
+enum Phase : int { kPhaseFP64 = 0, kPhaseSplit = 1, kPhaseRefine = 2 };
+
+struct State {
+  // solve parameters (written by the init kernel)
+  int n;
+  int ld;
+  int nocc;
+  int rule;
+  int maxiter;
+  int prec;
+  int fp64_prefix;
+  int slice_fmt;  // SliceFmt of the split products
+  double tol;
+  double emin_override;  // NaN = use Gershgorin
+  double emax_override;
+  // control state
+  double emin, emax;  // bounds used for X0
+  double t1, t2;      // Tr X_k and Tr X_k^2 = ||X_k||_F^2 of the current iterate
+  double idem;        // |t2 - t1|
+  int iter;           // products performed (k)
+  int done;           // 1: stop the loop
+  int converged;      // 1: idempotency below tol
+  int status;         // progress_status_t
+  int bit;            // branch of the next product (1: 2X - X^2)
+  int phase;          // Phase of the next product
+  int phase_iters[3];
+  int split_stall;    // consecutive split-phase steps without improvement
+  int x_fp64_valid;   // the current iterate X_k is stored in FP64 (buffer k % 2)
+  int x_slices_valid; // the current iterate X_k is stored as slices (set k % 2)
+  unsigned int ticket;  // CTA arrival counter of the running launch
+  double best_split_idem;
+  unsigned long long bits[4];
+  double idem_hist[kMaxHist];
+  double margin_hist[kMaxHist];
+};
+
+// ---------------------------------------------------------------------------
+// reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum of two doubles in a fixed order; result valid in thread 0.
+// `scratch` holds 2 * (blockDim.x / 32) doubles.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) {
+    scratch[wid] = a;
+    scratch[nw + wid] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      sa += scratch[w];
+      sb += scratch[nw + w];
+    }
+    a = sa;
+    b = sb;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SP2 control (§IV.A): convergence, divergence and the branch of the next
+// product, from the FP64 traces of the current iterate X_k.
+
+__device__ inline void decide(State* st) {
+  const int k = st->iter;
+  const double t1 = st->t1, t2 = st->t2;
+  const double n = (double)st->n;
+  const double idem = fabs(t2 - t1);
+  st->idem = idem;
+  if (k < kMaxHist) st->idem_hist[k] = idem;
+  // The mapped spectrum must stay in [0, 1]: then 0 <= Tr X <= n and
+  // Tr X^2 <= Tr X. A clear violation means the bounds did not enclose the
+  // spectrum (or the input was not finite).
+  const bool finite = isfinite(t1) && isfinite(t2);
+  const bool escaped = t1 < -1e-6 * n - 1e-3 || t1 > n * (1.0 + 1e-6) + 1e-3 ||
+                       t2 > t1 + 1e-3 * (n + 1.0);
+  if (!finite || escaped) {
+    st->status = PROGRESS_EBOUNDS;
+    st->done = 1;
+    return;
+  }
+  int phase = st->phase;
+  bool stalled = false;
+  if (st->prec == PROGRESS_FP64) {
+    phase = kPhaseFP64;
+  } else {
+    if (st->prec == PROGRESS_FP32_SPLIT) {
+      phase = kPhaseSplit;
+    } else if (phase == kPhaseFP64 && k >= st->fp64_prefix) {
+      // MIXED: the FP64 prefix is over, switch to split products.
+      phase = kPhaseSplit;
+      st->best_split_idem = idem;
+      st->split_stall = 0;
+    }
+    if (phase == kPhaseSplit && k > 0) {
+      // Low precision stops helping once the idempotency error reaches its
+      // round-off floor: two steps in a row without a 0.1 % improvement.
+      if (idem < st->best_split_idem * 0.999) {
+        st->best_split_idem = idem;
+        st->split_stall = 0;
+      } else if (++st->split_stall >= 2 && idem < 1.0) {
+        stalled = true;
+      }
+    }
+    if (stalled && st->prec != PROGRESS_FP32_SPLIT) phase = kPhaseRefine;  // MIXED
+  }
+  st->phase = phase;
+  if (stalled && st->prec == PROGRESS_FP32_SPLIT) {
+    // All-split mode: the round-off floor is the answer.
+    st->converged = 1;
+    st->done = 1;
+    return;
+  }
+  // Convergence is tested in FP64-accurate phases only.
+  if (phase != kPhaseSplit && idem < st->tol) {
+    st->converged = 1;
+    st->done = 1;
+    return;
+  }
+  if (k >= st->maxiter) {
+    st->status = PROGRESS_ENOCONV;
+    st->done = 1;
+    return;
+  }
+  const double nocc = (double)st->nocc;
+  int b;
+  double margin;
+  if (st->rule == PROGRESS_RULE_PAPER) {
+    margin = nocc - t1;
+    b = (t1 - nocc) <= 0.0 ? 1 : 0;
+  } else {
+    const double d_square = fabs(t2 - nocc);
+    const double d_expand = fabs(2.0 * t1 - t2 - nocc);
+    margin = d_square - d_expand;
+    b = margin > 1e-12 * fmax(n, 1.0) ? 1 : 0;
+  }
+  st->bit = b;
+  if (k < kMaxHist) {
+    st->margin_hist[k] = margin;
+    if (b) st->bits[k >> 6] |= 1ull << (k & 63);
+  }
+}
+
+// Ticket of a CTA that finished its tile; true for the last CTA of the grid.
+// Caller must have written its partials before, by thread 0.
+__device__ __forceinline__ bool last_cta_arrives(State* st, unsigned int total, int* flag_smem) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(&st->ticket, 1u);
+    *flag_smem = (t == total - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool last = *flag_smem != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Deterministic sum of `count` pairs (a, b) stored interleaved; valid in thread 0.
+__device__ inline void reduce_partials(const double* partials, int count, double& a, double& b,
+                                       double* scratch) {
+  double sa = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    sa += __ldcg(partials + 2 * i);
+    sb += __ldcg(partials + 2 * i + 1);
+  }
+  block_sum2(sa, sb, scratch);
+  a = sa;
+  b = sb;
+}
+
+}  // namespace sp2

@@ -1,0 +1,228 @@
+// O(n^2) kernels of the SP2 solver: state init, Gershgorin bounds (§VIII.A),
+// the X0 map (§IV.A) and the final copy of the converged iterate into D.
+// All are HBM-bound streams over the matrix; rows are read by whole warps
+// (coalesced), partial sums are combined in a fixed order.
+#include <math.h>
+
+#include "sp2_common.cuh"
+#include "sp2_launch.h"
+#include "sp2_slices.cuh"
+
+namespace sp2 {
+
+namespace {
+
+constexpr int kEwThreads = 256;
+constexpr int kEwMaxBlocks = 152 * 8;
+
+__global__ void init_kernel(State* st, SolveParams p) {
+  // zero the whole state, then write the parameters
+  const int words = sizeof(State) / sizeof(unsigned int);
+  unsigned int* w = reinterpret_cast<unsigned int*>(st);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) w[i] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->n = (int)p.n;
+    st->ld = p.ld;
+    st->nocc = (int)p.nocc;
+    st->rule = p.rule;
+    st->maxiter = p.maxiter;
+    st->prec = p.prec;
+    st->fp64_prefix = p.fp64_prefix;
+    st->slice_fmt = p.slice_fmt;
+    st->tol = p.tol;
+    st->emin_override = p.emin_override;
+    st->emax_override = p.emax_override;
+    st->best_split_idem = INFINITY;
+    st->phase = (p.prec == PROGRESS_FP32_SPLIT) ? kPhaseSplit : kPhaseFP64;
+  }
+}
+
+// One warp per row: R_i = sum_{j != i} |H_ij|; per-block min(H_ii - R_i) and
+// max(H_ii + R_i), then the last block combines the block results.
+__global__ void __launch_bounds__(kEwThreads) gershgorin_kernel(const double* __restrict__ H,
+                                                                int64_t n, State* st,
+                                                                double* __restrict__ blk,
+                                                                double* __restrict__ out) {
+  __shared__ double s_lo[kEwThreads / 32], s_hi[kEwThreads / 32];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (kEwThreads / 32);
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = (int64_t)blockIdx.x * (kEwThreads / 32) + wid; i < n; i += warps) {
+    const double* row = H + i * n;
+    double r = 0.0;
+    for (int64_t j = lane; j < n; j += 32) r += (j == i) ? 0.0 : fabs(row[j]);
+    r = warp_sum(r);
+    const double d = row[i];
+    lo = fmin(lo, d - r);
+    hi = fmax(hi, d + r);
+  }
+  lo = warp_min(lo);
+  hi = warp_max(hi);
+  if (lane == 0) {
+    s_lo[wid] = lo;
+    s_hi[wid] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kEwThreads / 32; ++w) {
+      lo = fmin(lo, s_lo[w]);
+      hi = fmax(hi, s_hi[w]);
+    }
+    blk[2 * blockIdx.x] = lo;
+    blk[2 * blockIdx.x + 1] = hi;
+  }
+  if (!last_cta_arrives(st, gridDim.x, &s_last)) return;
+  if (threadIdx.x == 0) {
+    lo = INFINITY;
+    hi = -INFINITY;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+      lo = fmin(lo, __ldcg(blk + 2 * b));
+      hi = fmax(hi, __ldcg(blk + 2 * b + 1));
+    }
+    double e0 = isnan(st->emin_override) ? lo : st->emin_override;
+    double e1 = isnan(st->emax_override) ? hi : st->emax_override;
+    // A zero-width enclosure (H = c I, or n = 1) leaves the X0 map undefined;
+    // widen it by 1 on each side, which still encloses the spectrum.
+    if (!(e1 > e0)) {
+      e0 -= 1.0;
+      e1 += 1.0;
+    }
+    st->emin = e0;
+    st->emax = e1;
+    if (out) {
+      out[0] = lo;
+      out[1] = hi;
+    }
+    st->ticket = 0u;
+  }
+}
+
+// X0 = (emax I - H) / (emax - emin) on the n x n block, zero padding up to
+// ld x ld; writes the FP64 iterate and/or its slices; reduces Tr X0 and
+// ||X0||_F^2 and decides the first product.
+template <int F>
+__global__ void __launch_bounds__(kEwThreads) x0_kernel(const double* __restrict__ H, State* st,
+                                                        double* __restrict__ X, Slices S,
+                                                        int write_fp64, int write_slices,
+                                                        double* __restrict__ partials) {
+  __shared__ double scratch[2 * kEwThreads / 32];
+  __shared__ int s_last;
+  const int64_t n = st->n;
+  const int ld = st->ld;
+  const double emax = st->emax, width = st->emax - st->emin;
+  double tr = 0.0, fr = 0.0;
+  for (int64_t r = blockIdx.x; r < ld; r += gridDim.x) {
+    for (int64_t c = threadIdx.x; c < ld; c += kEwThreads) {
+      const size_t idx = (size_t)r * ld + c;
+      double x = 0.0;
+      if (r < n && c < n) {
+        const double h = H[r * n + c];
+        x = ((r == c) ? (emax - h) : -h) / width;
+        if (r == c) tr += x;
+        fr += x * x;
+      }
+      if (write_fp64) X[idx] = x;
+      if (write_slices) store_slices<F>(S, idx, x);
+    }
+  }
+  block_sum2(tr, fr, scratch);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = tr;
+    partials[2 * blockIdx.x + 1] = fr;
+  }
+  if (!last_cta_arrives(st, gridDim.x, &s_last)) return;
+  double a, b;
+  reduce_partials(partials, gridDim.x, a, b, scratch);
+  if (threadIdx.x == 0) {
+    st->t1 = a;
+    st->t2 = b;
+    st->iter = 0;
+    st->x_fp64_valid = write_fp64;
+    st->x_slices_valid = write_slices;
+    st->ticket = 0u;
+    decide(st);
+  }
+}
+
+// D (n x n, leading dim n) <- the current iterate, from FP64 if it is stored
+// that way, else from its slices.
+template <int F>
+__global__ void __launch_bounds__(kEwThreads) finalize_kernel(const State* __restrict__ st,
+                                                              DevBuffers b, double* __restrict__ D,
+                                                              int64_t n) {
+  const int ld = st->ld;
+  const int k = st->iter & 1;
+  const bool from64 = st->x_fp64_valid != 0;
+  const double* X = b.x64[k];
+  const uint16_t* s0 = b.sl[k][0];
+  const uint16_t* s1 = b.sl[k][1];
+  const uint16_t* s2 = b.sl[k][2];
+  for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+    for (int64_t c = threadIdx.x; c < n; c += kEwThreads) {
+      const size_t src = (size_t)r * ld + c;
+      double v;
+      if (from64) {
+        v = X[src];
+      } else {
+        v = join_value_d<F>(s0[src], s1[src], F == kBF16x3 ? s2[src] : (uint16_t)0);
+      }
+      D[r * n + c] = v;
+    }
+  }
+}
+
+int ew_blocks(int64_t rows) {
+  int64_t b = rows;
+  if (b > kEwMaxBlocks) b = kEwMaxBlocks;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_init(const DevBuffers& b, const SolveParams& p, cudaStream_t s) {
+  init_kernel<<<1, 256, 0, s>>>(b.st, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gershgorin(const double* H, int64_t n, const DevBuffers& b, double* out,
+                              cudaStream_t s) {
+  int64_t blocks = (n + kEwThreads / 32 - 1) / (kEwThreads / 32);
+  if (blocks > kEwMaxBlocks) blocks = kEwMaxBlocks;
+  if (blocks > b.max_partials) blocks = b.max_partials;
+  gershgorin_kernel<<<(int)blocks, kEwThreads, 0, s>>>(H, n, b.st, b.partials, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x0(const double* H, const DevBuffers& b, const SolveParams& p, cudaStream_t s) {
+  const bool split_first =
+      p.prec == PROGRESS_FP32_SPLIT || (p.prec != PROGRESS_FP64 && p.fp64_prefix == 0);
+  const int write_fp64 = split_first ? 0 : 1;
+  const int write_slices = split_first ? 1 : 0;
+  int blocks = ew_blocks(p.ld);
+  if (blocks > b.max_partials) blocks = b.max_partials;
+  Slices S;
+  for (int i = 0; i < 3; ++i) S.s[i] = b.sl[0][i];
+  if (p.slice_fmt == kBF16x3)
+    x0_kernel<kBF16x3><<<blocks, kEwThreads, 0, s>>>(H, b.st, b.x64[0], S, write_fp64,
+                                                     write_slices, b.partials);
+  else
+    x0_kernel<kFP16x2><<<blocks, kEwThreads, 0, s>>>(H, b.st, b.x64[0], S, write_fp64,
+                                                     write_slices, b.partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const DevBuffers& b, double* D, int64_t n, int ld, int slice_fmt,
+                            cudaStream_t s) {
+  (void)ld;
+  const int blocks = ew_blocks(n);
+  if (slice_fmt == kBF16x3)
+    finalize_kernel<kBF16x3><<<blocks, kEwThreads, 0, s>>>(b.st, b, D, n);
+  else
+    finalize_kernel<kFP16x2><<<blocks, kEwThreads, 0, s>>>(b.st, b, D, n);
+  return cudaGetLastError();
+}
+
+}  // namespace sp2

@@ -1,0 +1,53 @@
+// Host-side launch wrappers of the SP2 kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sp2 {
+
+struct State;
+struct Slices;
+
+// Pointers of one workspace, as the kernels see them.
+struct DevBuffers {
+  State* st;
+  double* x64[2];        // FP64 ping-pong iterates, ld x ld
+  uint16_t* sl[2][3];    // slice ping-pong sets, ld x ld each
+  double* partials;      // per-CTA partial traces (2 doubles per CTA)
+  int max_partials;
+};
+
+struct SolveParams {
+  int64_t n;
+  int ld;
+  int64_t nocc;
+  int rule;
+  int maxiter;
+  int prec;
+  int fp64_prefix;
+  int slice_fmt;
+  double tol;
+  double emin_override, emax_override;
+};
+
+cudaError_t launch_init(const DevBuffers& b, const SolveParams& p, cudaStream_t s);
+// Gershgorin bounds into st->emin/emax (unless overridden) and, if out != null,
+// into out[0..1].
+cudaError_t launch_gershgorin(const double* H, int64_t n, const DevBuffers& b, double* out,
+                              cudaStream_t s);
+cudaError_t launch_x0(const double* H, const DevBuffers& b, const SolveParams& p, cudaStream_t s);
+// One FP64 product step (no-op unless the state says the next product is FP64).
+cudaError_t launch_square_fp64(const DevBuffers& b, int ld, int slice_fmt,
+                               unsigned long long cond_handle, cudaStream_t s);
+// One split-precision tcgen05 product step (no-op unless the next product is split).
+cudaError_t launch_square_split(const DevBuffers& b, const SolveParams& p,
+                                unsigned long long cond_handle, cudaStream_t s);
+bool split_tensor_maps_ready(const DevBuffers& b, int ld, int fmt);
+cudaError_t launch_finalize(const DevBuffers& b, double* D, int64_t n, int ld, int slice_fmt,
+                            cudaStream_t s);
+
+int fp64_tile_count(int ld);
+int split_tile_count(int ld);
+
+}  // namespace sp2

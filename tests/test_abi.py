@@ -1,0 +1,111 @@
+"""The C-ABI library builds, loads and exports every symbol the headers declare
+(no GPU needed: no compute call is made)."""
+
+import ctypes
+import glob
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_13772_gb300.build import build
+    build()
+    import paper_2401_13772_gb300 as pkg
+    return pkg.load()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(progress_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_headers_declare_the_boundary():
+    names = declared_functions()
+    for required in ("progress_gershgorin_bounds", "progress_sp2_dense", "progress_sp2_dense_ex"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2401_13772_gb300 import _lib
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"{name} has no ctypes signature"
+
+
+def test_struct_sizes_match_header_layout():
+    from paper_2401_13772_gb300 import _lib
+    # progress_opts_t: 4 int32, 2 double, 2 int32, 2 pointers, int32 reserved[4]
+    assert ctypes.sizeof(_lib.Opts) == 4 * 4 + 2 * 8 + 2 * 4 + 2 * 8 + 4 * 4
+    assert _lib.Opts.emin.offset == 16 and _lib.Opts.loop_mode.offset == 32
+    assert _lib.Opts.loop_events.offset == 40
+    # progress_info_t: 6 int32, 4 double, 4 uint64
+    assert ctypes.sizeof(_lib.Info) == 6 * 4 + 4 * 8 + 4 * 8
+    assert _lib.Info.emin.offset == 24 and _lib.Info.bits.offset == 56
+
+
+def test_defaults_and_version(lib):
+    from paper_2401_13772_gb300 import _lib
+    o = _lib.Opts()
+    lib.progress_opts_default(ctypes.byref(o))
+    assert o.prec == _lib.FP64 and o.rule == _lib.RULE_NEARER
+    assert o.maxiter == 100 and o.fp64_prefix == 12
+    assert math.isnan(o.emin) and math.isnan(o.emax)
+    assert lib.progress_version() == b"0.1.0"
+
+
+def test_argument_errors_before_any_device_work(lib):
+    from paper_2401_13772_gb300 import _lib
+    P = ctypes.c_void_p
+    # nocc out of range, negative n, negative tol: rejected before touching CUDA
+    assert lib.progress_sp2_dense(P(16), 8, 9, 1e-9, P(32), None) == _lib.EINVAL
+    assert lib.progress_sp2_dense(P(16), -1, 0, 1e-9, P(32), None) == _lib.EINVAL
+    assert lib.progress_sp2_dense(P(16), 8, 4, -1.0, P(32), None) == _lib.EINVAL
+    assert lib.progress_sp2_dense(P(16), 8, 4, 1e-9, P(16), None) == _lib.EINVAL  # D aliases H
+    lib.progress_sp2_dense(P(16), 8, 9, 1e-9, P(32), None)
+    assert b"nocc" in lib.progress_last_error()
+    o = _lib.Opts()
+    lib.progress_opts_default(ctypes.byref(o))
+    o.maxiter = 1000
+    assert lib.progress_sp2_dense_ex(P(16), 8, 4, 1e-9, P(32), ctypes.byref(o), None, None) == _lib.EINVAL
+    o.maxiter = 10
+    o.emin, o.emax = 1.0, 0.0
+    assert lib.progress_sp2_dense_ex(P(16), 8, 4, 1e-9, P(32), ctypes.byref(o), None, None) == _lib.EINVAL
+    assert lib.progress_gershgorin_bounds(P(16), 0, P(32), None) == _lib.EINVAL
+    assert b"n < 1" in lib.progress_last_error()
+    # n = 0 is a no-op
+    info = _lib.Info()
+    assert lib.progress_sp2_dense_ex(None, 0, 0, 1e-9, None, None, ctypes.byref(info), None) == _lib.OK
+    assert info.converged == 1
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The package never imports the oracle and fails loudly without the library."""
+    pkg_dir = os.path.join(ROOT, "paper_2401_13772_gb300")
+    for f in glob.glob(os.path.join(pkg_dir, "*.py")):
+        src = open(f).read()
+        assert "import oracle" not in src and "from oracle" not in src, f
+    from paper_2401_13772_gb300 import _lib
+    old = os.environ.get("PROGRESS_SP2_LIB")
+    saved = _lib._lib
+    try:
+        os.environ["PROGRESS_SP2_LIB"] = "/nonexistent/libprogress_sp2.so"
+        _lib._lib = None
+        with pytest.raises(RuntimeError, match="missing"):
+            _lib.load()
+    finally:
+        _lib._lib = saved
+        if old is None:
+            os.environ.pop("PROGRESS_SP2_LIB", None)
+        else:
+            os.environ["PROGRESS_SP2_LIB"] = old

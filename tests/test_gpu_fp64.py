@@ -1,0 +1,166 @@
+"""FP64 SP2 on the GPU through the C ABI, element by element against the CPU oracle."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import chain_hamiltonian, cube_hamiltonian
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-10  # max |D - D_ref| gate of the FP64 path
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a CUDA device"
+    from paper_2401_13772_gb300.build import build
+    build()
+    import paper_2401_13772_gb300 as p
+    p.load()
+    return p
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def test_gershgorin_matches_oracle(pkg):
+    for H in (chain_hamiltonian(512)[0], cube_hamiltonian(70, 1)[0], np.array([[3.5]])):
+        b = host(pkg.gershgorin_bounds(dev(H)))
+        emin, emax = oracle.gershgorin_bounds(H)
+        assert abs(b[0] - emin) <= 1e-12 * max(1.0, abs(emin))
+        assert abs(b[1] - emax) <= 1e-12 * max(1.0, abs(emax))
+
+
+def test_chain_512_matches_projector_and_golden_bits(pkg):
+    H, nocc = chain_hamiltonian(512, -1.0, -0.6)
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "chain512_sp2.json")))
+    w, V = oracle.jacobi_eigh(H)
+    Dref, _ = oracle.density_projector(w, V, nocc)
+    for rule in ("nearer", "paper"):
+        for loop_mode in (0, 1):
+            D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-12, rule=rule, loop_mode=loop_mode)
+            assert info["status"] == "OK" and info["converged"]
+            assert info["iters"] == g[rule]["iters"]
+            assert "".join(map(str, info["bits"])) == g[rule]["bits"]
+            assert info["emin"] == -1.6 and info["emax"] == 1.6
+            assert np.abs(host(D) - Dref).max() <= TOL_FP64
+
+
+@pytest.mark.parametrize("sites,seed", [(32, 1), (75, 2), (128, 3), (250, 4)])
+def test_cube_ragged_sizes_match_projector(pkg, sites, seed):
+    # n = 128, 300, 512, 1000: one tile, several tiles with a ragged tail
+    H, nocc = cube_hamiltonian(sites, seed)
+    w, V = oracle.jacobi_eigh(H)
+    Dref, gap = oracle.density_projector(w, V, nocc)
+    D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-12)
+    assert info["status"] == "OK" and info["converged"], info
+    assert np.abs(host(D) - Dref).max() <= TOL_FP64
+    ref = oracle.sp2_plain(H, nocc, 1e-12)
+    assert abs(info["iters"] - ref["iters"]) <= 1
+
+
+def test_intermediate_iterates_match_plain_sp2(pkg):
+    # maxiter = k stops with ENOCONV and leaves X_k in D
+    H, nocc = cube_hamiltonian(75, 5)  # n = 300
+    for k in (1, 2, 7, 20):
+        D, info = pkg.sp2_dense_ex(dev(H), nocc, 0.0, maxiter=k, raise_on_status=False)
+        assert info["status"] == "ENOCONV" and info["iters"] == k
+        ref = oracle.sp2_plain(H, nocc, 0.0, stop_after=k)
+        assert info["bits"] == ref["bits"]
+        assert np.abs(host(D) - ref["D"]).max() <= 1e-12
+        assert abs(info["trace"] - ref["t1"][-1]) <= 1e-9
+
+
+def test_degenerate_cases(pkg):
+    import torch
+    H, _ = cube_hamiltonian(16, 9)  # n = 64
+    n = H.shape[0]
+    D, info = pkg.sp2_dense_ex(dev(H), 0, 1e-12)
+    assert info["converged"] and np.abs(host(D)).max() <= 1e-12
+    D, info = pkg.sp2_dense_ex(dev(H), n, 1e-12)
+    assert info["converged"] and np.abs(host(D) - np.eye(n)).max() <= 1e-12
+    # 1 x 1
+    D, info = pkg.sp2_dense_ex(dev(np.array([[0.7]])), 1, 1e-12)
+    assert abs(host(D)[0, 0] - 1.0) <= 1e-12
+    D, info = pkg.sp2_dense_ex(dev(np.array([[0.7]])), 0, 1e-12)
+    assert abs(host(D)[0, 0]) <= 1e-12
+    # diagonal H: exact occupation of the nocc lowest levels
+    d = np.random.default_rng(3).permutation(np.linspace(-2.0, 3.0, 200))
+    D, info = pkg.sp2_dense_ex(dev(np.diag(d)), 77, 1e-13)
+    expect = np.zeros(200)
+    expect[np.argsort(d)[:77]] = 1.0
+    assert np.abs(host(D) - np.diag(expect)).max() <= 1e-12
+    # n = 0
+    z = torch.empty((0, 0), dtype=torch.float64, device="cuda:0")
+    D, info = pkg.sp2_dense_ex(z, 0, 1e-12)
+    assert info["converged"]
+
+
+def test_bad_bounds_and_nonfinite_input_report_status(pkg):
+    H, nocc = cube_hamiltonian(32, 2)
+    emin, emax = oracle.gershgorin_bounds(H)
+    w = np.linalg.eigvalsh(H)
+    # bounds that cut the spectrum: the iterate leaves [0, 1]
+    D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-12, emin=w[3], emax=w[-3],
+                               raise_on_status=False)
+    assert info["status"] in ("EBOUNDS", "ENOCONV")
+    Hn = H.copy()
+    Hn[3, 5] = Hn[5, 3] = np.nan
+    D, info = pkg.sp2_dense_ex(dev(Hn), nocc, 1e-12, raise_on_status=False)
+    assert info["status"] == "EBOUNDS"
+    # the library stays usable afterwards
+    D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-12)
+    assert info["converged"]
+    # tighter (exact) bounds are accepted and converge to the same D
+    D1, i1 = pkg.sp2_dense_ex(dev(H), nocc, 1e-12, emin=w[0], emax=w[-1])
+    D2, i2 = pkg.sp2_dense_ex(dev(H), nocc, 1e-12)
+    assert np.abs(host(D1) - host(D2)).max() <= 1e-10
+    assert i1["iters"] <= i2["iters"]
+
+
+def test_async_entry_point_and_query(pkg):
+    import torch
+    H, nocc = cube_hamiltonian(64, 11)
+    Hd = dev(H)
+    D = pkg.sp2_dense(Hd, nocc, 1e-12)
+    from paper_2401_13772_gb300 import _lib
+    import ctypes
+    info = _lib.Info()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert pkg.load().progress_sp2_query(s, ctypes.byref(info)) == _lib.OK
+    assert info.converged == 1
+    ref = oracle.sp2_plain(H, nocc, 1e-12)
+    assert np.abs(host(D) - ref["D"]).max() <= TOL_FP64
+    # in place (dD == dH) is allowed in the _ex entry point
+    Hd2 = dev(H)
+    out, _ = pkg.sp2_dense_ex(Hd2, nocc, 1e-12, D=Hd2)
+    assert np.abs(host(out) - ref["D"]).max() <= TOL_FP64
+
+
+def test_streams_are_independent(pkg):
+    import torch
+    H1, n1 = cube_hamiltonian(40, 1)
+    H2, n2 = chain_hamiltonian(256)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    A1, A2 = dev(H1), dev(H2)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        D1 = pkg.sp2_dense(A1, n1, 1e-12, stream=s1)
+    with torch.cuda.stream(s2):
+        D2 = pkg.sp2_dense(A2, n2, 1e-12, stream=s2)
+    torch.cuda.synchronize()
+    assert np.abs(host(D1) - oracle.sp2_plain(H1, n1, 1e-12)["D"]).max() <= TOL_FP64
+    assert np.abs(host(D2) - oracle.sp2_plain(H2, n2, 1e-12)["D"]).max() <= TOL_FP64
+    pkg.release(s1)
+    pkg.release(s2)

@@ -351,3 +351,12 @@ def test_golden_chain_fixture_matches_closed_form_facts():
     assert g["paper"]["bits"] == "".join("1" if c == "0" else "0" for c in g["nearer"]["bits"])
     H, nocc = chain_hamiltonian(512, T1, T2)
     assert "".join(map(str, oracle.sp2_plain(H, nocc, 1e-12)["bits"])) == g["nearer"]["bits"]
+
+
+def test_sp2_scalar_and_multiple_of_identity():
+    # zero-width Gershgorin interval: the occupation is still exact
+    for nocc in (0, 1):
+        out = oracle.sp2_plain(np.array([[0.7]]), nocc, 1e-14)
+        assert out["converged"] and abs(out["D"][0, 0] - nocc) < 1e-14
+    out = oracle.sp2_plain(2.5 * np.eye(6), 6, 1e-14)
+    assert np.abs(out["D"] - np.eye(6)).max() < 1e-14
