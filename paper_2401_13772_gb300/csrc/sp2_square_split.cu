@@ -1,18 +1,529 @@
-// Split-precision SP2 product step on tcgen05 tensor cores (placeholder).
+// Split-precision SP2 product step on the sm_103a tcgen05 tensor cores.
+//
+// One CTA computes one 128 x 128 upper-triangle tile (I <= J) of S = X*X for
+// the symmetric iterate X. X is held as 16-bit operand slices (FP16x2: hi, lo
+// scaled by 2^11; BF16x3: hi, mid, lo), each an ld x ld row-major matrix, so
+// both operands of tile (I, J) are K-major row panels of the same slices.
+//
+//   warp 0, one lane : TMA producer -- 128 x 64 slice boxes (128 B rows,
+//                      128 B swizzle) of the I and J row panels into a
+//                      STAGES-deep shared-memory ring (mbarrier complete_tx)
+//   warp 1, one lane : MMA issuer -- tcgen05.mma kind::f16, M = N = 128,
+//                      K = 16, FP32 accumulators in tensor memory:
+//                      acc0 += hi*hi^T, acc1 += the cross products
+//                      (FP16x2: hi*lo^T + lo*hi^T; BF16x3: hi*mid^T + mid*hi^T
+//                      + hi*lo^T + lo*hi^T + mid*mid^T); tcgen05.commit frees a
+//                      stage and finally signals the epilogue
+//   all 4 warps      : epilogue -- tcgen05.ld of the lane (row) each thread
+//                      owns, S = acc0 + scale * acc1, the SP2 branch of §IV.A
+//                      chosen on the device (X' = S or 2X - S), the new slices
+//                      of X' at (r, c) and at the mirror (c, r), FP64 X' when
+//                      the precision schedule may leave the split phase next,
+//                      and FP64 partial traces Tr X', ||X'||_F^2.
+//
+// Every mbarrier wait is bounded; a wait that runs out records
+// PROGRESS_ETIMEOUT in the solve state, stops the loop and the CTA still frees
+// its tensor memory before it exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <stdio.h>
+
 #include "sp2_common.cuh"
 #include "sp2_launch.h"
+#include "sp2_slices.cuh"
 
 namespace sp2 {
 
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int BK = 64;                         // 16-bit elements = 128 B rows
+constexpr int TILE_BYTES = BM * BK * 2;        // one 128 x 64 slice box (16 KB)
+constexpr int THREADS = 128;
+constexpr int TMEM_COLS = 256;                 // acc0 | acc1, 128 columns each
+constexpr unsigned kWaitLimit = 1u << 26;      // try_wait polls before giving up
+
+template <int F>
+struct Cfg {
+  static constexpr int NS = (F == kFP16x2) ? 2 : 3;                 // slices
+  static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;            // A and B boxes
+  static constexpr int STAGES = (F == kFP16x2) ? 3 : 2;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;    // + align + barriers
+};
+
+struct TensorMaps {
+  CUtensorMap m[2][3];  // [ping-pong set][slice]
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; false (and *err set) when the limit runs out. With
+// abort_on_err it also gives up as soon as another role has failed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* err,
+                                          bool abort_on_err = true, unsigned limit = kWaitLimit) {
+  for (unsigned i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (abort_on_err && *err) return false;
+  }
+  *err = 1;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                   dst_smem),
+               "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+      : "memory");
+}
+
+// 32 lanes x 32 columns of 32-bit values: this thread's lane, 32 columns.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128 B swizzle, 8-row
+// swizzle atoms of 1024 B (stride byte offset), sm_100-family version bit.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, A/B type (0 f16, 1 bf16),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int ab_type, int m, int n) {
+  return (1u << 4) | ((uint32_t)ab_type << 7) | ((uint32_t)ab_type << 10) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tri_tile(int t, int T, int& I, int& J) {
+  const double b = 2.0 * T + 1.0;
+  int i = (int)floor((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
+  if (i < 0) i = 0;
+  while (i > 0 && i * T - i * (i - 1) / 2 > t) --i;
+  while ((i + 1) * T - (i + 1) * i / 2 <= t) ++i;
+  I = i;
+  J = i + (t - (i * T - i * (i - 1) / 2));
+}
+
+template <int F>
+__device__ __forceinline__ void pack_store_row(uint16_t* const* dst, size_t off, const float* x) {
+  // 32 consecutive values of one row -> slices, 16-byte stores
+  uint32_t w[3][16];
+#pragma unroll
+  for (int j = 0; j < 32; j += 2) {
+    uint16_t a0, b0, c0, a1, b1, c1;
+    split_value_f<F>(x[j], a0, b0, c0);
+    split_value_f<F>(x[j + 1], a1, b1, c1);
+    w[0][j / 2] = (uint32_t)a0 | ((uint32_t)a1 << 16);
+    w[1][j / 2] = (uint32_t)b0 | ((uint32_t)b1 << 16);
+    w[2][j / 2] = (uint32_t)c0 | ((uint32_t)c1 << 16);
+  }
+#pragma unroll
+  for (int s = 0; s < Cfg<F>::NS; ++s) {
+    uint4* p = reinterpret_cast<uint4*>(dst[s] + off);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      p[q] = make_uint4(w[s][4 * q], w[s][4 * q + 1], w[s][4 * q + 2], w[s][4 * q + 3]);
+  }
+}
+
+template <int F>
+__global__ void __launch_bounds__(THREADS, 1)
+    square_split_kernel(const __grid_constant__ TensorMaps maps, DevBuffers buf,
+                        unsigned long long cond) {
+  using C = Cfg<F>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_err;
+  __shared__ int s_consumed;
+  __shared__ int s_last;
+  __shared__ double s_scratch[2 * THREADS / 32];
+
+  State* st = buf.st;
+  const int done = __ldcg(&st->done);
+  const int phase = __ldcg(&st->phase);
+  if (done) {
+    if (cond && blockIdx.x == 0 && threadIdx.x == 0)
+      cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+    return;
+  }
+  if (phase != kPhaseSplit) return;  // the FP64 kernel owns this step
+  const int k_iter = __ldcg(&st->iter);
+  const int bit = __ldcg(&st->bit);
+  const int ld = st->ld;
+  // FP64 X' is needed if the schedule may switch to FP64 refinement after
+  // this product (MIXED: the split phase has stalled once already).
+  const bool want_fp64 = (st->prec == PROGRESS_MIXED_FP16 || st->prec == PROGRESS_MIXED_BF16) &&
+                         __ldcg(&st->split_stall) >= 1;
+  const int src = k_iter & 1, dst = (k_iter + 1) & 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int T = ld / BM;
+  int I, J;
+  tri_tile(blockIdx.x, T, I, J);
+  const int row_a = I * BM, row_b = J * BN;
+
+  // shared memory: stage ring (1024-aligned), then barriers
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t bars = base + C::STAGES * C::STAGE_BYTES;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (C::STAGES + s); };
+  const uint32_t accum_bar = bars + 8u * (2 * C::STAGES);
+
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    s_consumed = 0;
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(accum_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  volatile int* err = &s_err;
+
+  const int KB = ld / BK;
+  int issued = 0;  // k-blocks whose loads were issued (producer thread)
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer
+      for (int kb = 0; kb < KB; ++kb, ++issued) {
+        const int s = kb % C::STAGES;
+        const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+        if (!mbar_wait(empty_bar(s), ph ^ 1u, err)) break;
+        mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
+        const uint32_t sa = base + s * C::STAGE_BYTES;
+#pragma unroll
+        for (int j = 0; j < C::NS; ++j) {
+          tma_load_2d(sa + j * TILE_BYTES, &maps.m[src][j], kb * BK, row_a, full_bar(s));
+          tma_load_2d(sa + (C::NS + j) * TILE_BYTES, &maps.m[src][j], kb * BK, row_b,
+                      full_bar(s));
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      constexpr uint32_t idesc = idesc_f16(F == kBF16x3 ? 1 : 0, BM, BN);
+      const uint32_t acc0 = tmem, acc1 = tmem + 128;
+      bool ok = true;
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        const int s = kb % C::STAGES;
+        const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+        if (!mbar_wait(full_bar(s), ph, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = base + s * C::STAGE_BYTES;
+        uint64_t a[3], b[3];
+#pragma unroll
+        for (int j = 0; j < C::NS; ++j) {
+          a[j] = smem_desc_sw128(sa + j * TILE_BYTES);
+          b[j] = smem_desc_sw128(sa + (C::NS + j) * TILE_BYTES);
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 32 B per K = 16 step
+          const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+          mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, first);
+          mma_f16(acc1, a[0] + adv, b[1] + adv, idesc, first);
+          mma_f16(acc1, a[1] + adv, b[0] + adv, idesc, 1u);
+          if (F == kBF16x3) {
+            mma_f16(acc1, a[0] + adv, b[2] + adv, idesc, 1u);
+            mma_f16(acc1, a[2] + adv, b[0] + adv, idesc, 1u);
+            mma_f16(acc1, a[1] + adv, b[1] + adv, idesc, 1u);
+          }
+        }
+        mma_commit(empty_bar(s));  // frees the stage once these MMAs have read it
+        s_consumed = kb + 1;
+      }
+      mma_commit(accum_bar);  // all MMAs issued so far are complete -> epilogue
+    }
+    __syncwarp();
+  }
+
+  // ---- epilogue: every thread owns TMEM lane = tile row threadIdx.x
+  // (the MMA thread always commits accum_bar, so this wait does not abort
+  // early: no MMA may still be writing tensor memory past it)
+  const bool ok = mbar_wait(accum_bar, 0u, err, false);
+  tc_fence_after();
+  double tr = 0.0, fr = 0.0;
+  if (ok && *err == 0) {
+    const int r = row_a + threadIdx.x;
+    const float scale = (F == kFP16x2) ? kLoUnscale : 1.0f;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint16_t* xs0 = buf.sl[src][0];
+    const uint16_t* xs1 = buf.sl[src][1];
+    const uint16_t* xs2 = buf.sl[src][2];
+    uint16_t* out[3] = {buf.sl[dst][0], buf.sl[dst][1], buf.sl[dst][2]};
+    double* out64 = buf.x64[dst];
+    const bool diag = (I == J);
+#pragma unroll 1
+    for (int ch = 0; ch < BN / 32; ++ch) {
+      float v0[32], v1[32];
+      tmem_ld32(lane_addr + ch * 32, v0);
+      tmem_ld32(lane_addr + 128 + ch * 32, v1);
+      tmem_ld_wait();
+      const int c0 = row_b + ch * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = c0 + j;
+        float x = v0[j] + v1[j] * scale;
+        if (bit) {
+          const size_t m = (size_t)c * ld + r;  // X is symmetric: read the mirror (coalesced)
+          const float xo =
+              join_value<F>(xs0[m], xs1[m], F == kBF16x3 ? xs2[m] : (uint16_t)0);
+          x = 2.0f * xo - x;
+        }
+        v0[j] = x;
+        if (r <= c) {
+          const double xd = (double)x;
+          if (r == c) {
+            tr += xd;
+            fr += xd * xd;
+          } else {
+            fr += 2.0 * xd * xd;
+            // mirror (c, r): consecutive threads write consecutive r
+            const size_t m = (size_t)c * ld + r;
+            uint16_t a, b2, c2;
+            split_value_f<F>(x, a, b2, c2);
+            out[0][m] = a;
+            out[1][m] = b2;
+            if (F == kBF16x3) out[2][m] = c2;
+            if (want_fp64) out64[m] = xd;
+          }
+        }
+      }
+      // direct (r, c0..c0+31)
+      const size_t d = (size_t)r * ld + c0;
+      if (!diag) {
+        pack_store_row<F>(out, d, v0);
+        if (want_fp64) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) out64[d + j] = (double)v0[j];
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (r <= c0 + j) {
+            uint16_t a, b2, c2;
+            split_value_f<F>(v0[j], a, b2, c2);
+            out[0][d + j] = a;
+            out[1][d + j] = b2;
+            if (F == kBF16x3) out[2][d + j] = c2;
+            if (want_fp64) out64[d + j] = (double)v0[j];
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*err) {
+    // failure path: let TMA copies still in flight land before the CTA exits
+    if (threadIdx.x == 0) {
+      for (int kb = s_consumed; kb < issued; ++kb)
+        mbar_wait(full_bar(kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, err, false,
+                  kWaitLimit >> 4);
+    }
+    __syncthreads();
+  }
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+  if (*err && threadIdx.x == 0) {
+    st->status = PROGRESS_ETIMEOUT;
+    st->done = 1;
+  }
+
+  block_sum2(tr, fr, s_scratch);
+  if (threadIdx.x == 0) {
+    buf.partials[2 * blockIdx.x] = tr;
+    buf.partials[2 * blockIdx.x + 1] = fr;
+  }
+  if (!last_cta_arrives(st, gridDim.x, &s_last)) return;
+  double a, b;
+  reduce_partials(buf.partials, gridDim.x, a, b, s_scratch);
+  if (threadIdx.x == 0) {
+    st->ticket = 0u;
+    if (st->status == PROGRESS_ETIMEOUT) {
+      st->done = 1;
+    } else {
+      st->t1 = a;
+      st->t2 = b;
+      st->iter = k_iter + 1;
+      st->phase_iters[kPhaseSplit] += 1;
+      st->x_fp64_valid = want_fp64 ? 1 : 0;
+      st->x_slices_valid = 1;
+      decide(st);
+    }
+    if (st->done && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool encode_maps(const DevBuffers& b, int ld, int fmt, TensorMaps* maps) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = get_encoder();
+  if (!enc) return false;
+  const int ns = (fmt == kFP16x2) ? 2 : 3;
+  memset(maps, 0, sizeof *maps);
+  for (int k = 0; k < 2; ++k) {
+    for (int j = 0; j < ns; ++j) {
+      if (!b.sl[k][j]) return false;
+      cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ld};
+      cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+      cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+      cuuint32_t estr[2] = {1, 1};
+      CUresult r = enc(&maps->m[k][j],
+                       fmt == kFP16x2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                       2, (void*)b.sl[k][j], dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return false;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
 int split_tile_count(int ld) {
-  const int T = ld / 128;
+  const int T = ld / BM;
   return T * (T + 1) / 2;
+}
+
+bool split_tensor_maps_ready(const DevBuffers& b, int ld, int fmt) {
+  TensorMaps m;
+  return encode_maps(b, ld, fmt, &m);
 }
 
 cudaError_t launch_square_split(const DevBuffers& b, const SolveParams& p,
                                 unsigned long long cond_handle, cudaStream_t s) {
-  (void)b; (void)p; (void)cond_handle; (void)s;
-  return cudaErrorNotSupported;
+  const int ld = p.ld;
+  if (ld % BM) return cudaErrorInvalidValue;
+  const int tiles = split_tile_count(ld);
+  if (tiles > b.max_partials) return cudaErrorInvalidValue;
+  TensorMaps maps;
+  if (!encode_maps(b, ld, p.slice_fmt, &maps)) return cudaErrorInvalidValue;
+  if (p.slice_fmt == kBF16x3) {
+    const int smem = Cfg<kBF16x3>::SMEM;
+    cudaFuncSetAttribute(square_split_kernel<kBF16x3>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    square_split_kernel<kBF16x3><<<tiles, THREADS, smem, s>>>(maps, b, cond_handle);
+  } else {
+    const int smem = Cfg<kFP16x2>::SMEM;
+    cudaFuncSetAttribute(square_split_kernel<kFP16x2>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    square_split_kernel<kFP16x2><<<tiles, THREADS, smem, s>>>(maps, b, cond_handle);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace sp2
