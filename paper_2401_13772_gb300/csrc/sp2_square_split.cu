@@ -42,7 +42,7 @@ constexpr int BK = 64;                         // 16-bit elements = 128 B rows
 constexpr int TILE_BYTES = BM * BK * 2;        // one 128 x 64 slice box (16 KB)
 constexpr int THREADS = 128;
 constexpr int TMEM_COLS = 256;                 // acc0 | acc1, 128 columns each
-constexpr unsigned kWaitLimit = 1u << 26;      // try_wait polls before giving up
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait gives up after 2 s
 
 template <int F>
 struct Cfg {
@@ -86,16 +86,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; false (and *err set) when the limit runs out. With
-// abort_on_err it also gives up as soon as another role has failed.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: false (and *err set) once limit_ns of wall time have passed.
+// With abort_on_err it also gives up as soon as another role has failed.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* err,
-                                          bool abort_on_err = true, unsigned limit = kWaitLimit) {
-  for (unsigned i = 0; i < limit; ++i) {
+                                          bool abort_on_err = true,
+                                          uint64_t limit_ns = kWaitLimitNs) {
+  uint64_t t0 = 0;
+  for (unsigned i = 0;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if (abort_on_err && *err) return false;
+    if ((i & 255u) == 0u) {
+      const uint64_t t = global_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > limit_ns) {
+        *err = 1;
+        return false;
+      }
+    }
   }
-  *err = 1;
-  return false;
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
@@ -420,7 +435,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
       for (int kb = s_consumed; kb < issued; ++kb)
         mbar_wait(full_bar(kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, err, false,
-                  kWaitLimit >> 4);
+                  kWaitLimitNs / 10);
     }
     __syncthreads();
   }
