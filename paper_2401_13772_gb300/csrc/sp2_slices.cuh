@@ -1,11 +1,27 @@
 // Operand slices of the split-precision products.
 //
-// A split product represents each entry x of the iterate by 16-bit slices so
-// that X*X runs on the fp16/bf16 tensor cores with FP32 accumulation:
-//   FP16x2: hi = rn_fp16(x), lo = rn_fp16((x - hi) * 2^11)          (22 bits)
-//   BF16x3: hi = rn_bf16(x), mid = rn_bf16(x - hi), lo = rn_bf16(x - hi - mid)
-// (24 bits). Each slice is an ld x ld row-major matrix; for the symmetric X a
-// row panel is the K-major operand of both sides of the product.
+// Every iterate X of SP2 is symmetric with its spectrum in [0, 1], so every
+// entry has |x| <= 1 and every row has Euclidean norm <= 1. The slices are
+// therefore FIXED-POINT with one global scale (no per-row exponents):
+//
+//   FP16x2: hi = rint(x 2^11)              integer, |hi| <= 2^11 (exact in fp16)
+//           lo = rn_fp16((x 2^11 - hi) 2^11)   |lo| <= 2^10, 11 significant bits
+//           x ~ 2^-11 hi + 2^-22 lo        (absolute error <= 2^-23)
+//   BF16x3: hi  = rint(x 2^8)              integer, |hi| <= 2^8 (exact in bf16)
+//           mid = rint((x 2^8 - hi) 2^8)   integer, |mid| <= 2^7 (exact in bf16)
+//           lo  = rn_bf16(((x 2^8 - hi) 2^8 - mid) 2^8)
+//           x ~ 2^-8 hi + 2^-16 mid + 2^-24 lo  (absolute error <= 2^-26)
+//
+// Why fixed point: in S_ij = sum_k x_ik x_jk the leading group sum_k hi_ik hi_jk
+// is a sum of integer products bounded, by Cauchy-Schwarz and the row-norm
+// bound, by 2^22 (FP16x2) or 2^16 (BF16x3) plus rounding slack -- below 2^24,
+// so the tensor core's FP32 accumulation of that group is EXACT whatever its
+// internal rounding. Only the small correction groups see FP32 rounding. With
+// floating-point hi slices the leading group would carry the accumulator's
+// truncation error over K/16 steps.
+//
+// Each slice is an ld x ld row-major matrix; for the symmetric X a row panel
+// is the K-major operand of both sides of the product.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -16,76 +32,97 @@ namespace sp2 {
 
 enum SliceFmt : int { kFP16x2 = 0, kBF16x3 = 1 };
 
-constexpr float kLoScale = 2048.0f;          // 2^11, FP16x2 lo scaling
-constexpr float kLoUnscale = 1.0f / 2048.0f;
-
 struct Slices {
   uint16_t* s[3];  // hi, lo (FP16x2) or hi, mid, lo (BF16x3); row-major, leading dim ld
 };
 
 __device__ __forceinline__ uint16_t h_bits(__half h) { return __half_as_ushort(h); }
 __device__ __forceinline__ uint16_t b_bits(__nv_bfloat16 b) { return __bfloat16_as_ushort(b); }
-
-// Split a double into the slices of format F (packed as 16-bit patterns).
-template <int F>
-__device__ __forceinline__ void split_value(double x, uint16_t& a, uint16_t& b, uint16_t& c) {
-  if (F == kFP16x2) {
-    __half h = __double2half(x);
-    double r = (x - (double)__half2float(h)) * (double)kLoScale;
-    a = h_bits(h);
-    b = h_bits(__double2half(r));
-    c = 0;
-  } else {
-    __nv_bfloat16 h = __double2bfloat16(x);
-    double r1 = x - (double)__bfloat162float(h);
-    __nv_bfloat16 m = __double2bfloat16(r1);
-    double r2 = r1 - (double)__bfloat162float(m);
-    a = b_bits(h);
-    b = b_bits(m);
-    c = b_bits(__double2bfloat16(r2));
-  }
+__device__ __forceinline__ float h_val(uint16_t u) { return __half2float(__ushort_as_half(u)); }
+__device__ __forceinline__ float b_val(uint16_t u) {
+  return __bfloat162float(__ushort_as_bfloat16(u));
 }
 
+// Split x (|x| <= 1) into the slices of format F (16-bit patterns).
 template <int F>
 __device__ __forceinline__ void split_value_f(float x, uint16_t& a, uint16_t& b, uint16_t& c) {
   if (F == kFP16x2) {
-    __half h = __float2half_rn(x);
-    a = h_bits(h);
-    b = h_bits(__float2half_rn((x - __half2float(h)) * kLoScale));
+    const float y = x * 2048.0f;  // exact scaling
+    const float h = rintf(y);
+    a = h_bits(__float2half_rn(h));                        // integer, exact
+    b = h_bits(__float2half_rn((y - h) * 2048.0f));        // y - h exact (Sterbenz range)
     c = 0;
   } else {
-    __nv_bfloat16 h = __float2bfloat16_rn(x);
-    float r1 = x - __bfloat162float(h);
-    __nv_bfloat16 m = __float2bfloat16_rn(r1);
-    float r2 = r1 - __bfloat162float(m);
-    a = b_bits(h);
-    b = b_bits(m);
-    c = b_bits(__float2bfloat16_rn(r2));
+    const float y = x * 256.0f;
+    const float h = rintf(y);
+    const float r1 = (y - h) * 256.0f;
+    const float m = rintf(r1);
+    a = b_bits(__float2bfloat16_rn(h));
+    b = b_bits(__float2bfloat16_rn(m));
+    c = b_bits(__float2bfloat16_rn((r1 - m) * 256.0f));
   }
 }
 
-// Value represented by the slices.
+template <int F>
+__device__ __forceinline__ void split_value(double x, uint16_t& a, uint16_t& b, uint16_t& c) {
+  if (F == kFP16x2) {
+    const double y = x * 2048.0;
+    const double h = rint(y);
+    a = h_bits(__double2half(h));
+    b = h_bits(__double2half((y - h) * 2048.0));
+    c = 0;
+  } else {
+    const double y = x * 256.0;
+    const double h = rint(y);
+    const double r1 = (y - h) * 256.0;
+    const double m = rint(r1);
+    a = b_bits(__double2bfloat16(h));
+    b = b_bits(__double2bfloat16(m));
+    c = b_bits(__double2bfloat16((r1 - m) * 256.0));
+  }
+}
+
+// Value represented by the slices (FP32).
 template <int F>
 __device__ __forceinline__ float join_value(uint16_t a, uint16_t b, uint16_t c) {
   if (F == kFP16x2) {
-    return __half2float(__ushort_as_half(a)) + __half2float(__ushort_as_half(b)) * kLoUnscale;
+    return h_val(a) * (1.0f / 2048.0f) + h_val(b) * (1.0f / 4194304.0f);
   } else {
-    return __bfloat162float(__ushort_as_bfloat16(a)) +
-           (__bfloat162float(__ushort_as_bfloat16(b)) + __bfloat162float(__ushort_as_bfloat16(c)));
+    return b_val(a) * (1.0f / 256.0f) +
+           (b_val(b) * (1.0f / 65536.0f) + b_val(c) * (1.0f / 16777216.0f));
   }
 }
 
 template <int F>
 __device__ __forceinline__ double join_value_d(uint16_t a, uint16_t b, uint16_t c) {
   if (F == kFP16x2) {
-    return (double)__half2float(__ushort_as_half(a)) +
-           (double)__half2float(__ushort_as_half(b)) * (double)kLoUnscale;
+    return (double)h_val(a) * (1.0 / 2048.0) + (double)h_val(b) * (1.0 / 4194304.0);
   } else {
-    return (double)__bfloat162float(__ushort_as_bfloat16(a)) +
-           (double)__bfloat162float(__ushort_as_bfloat16(b)) +
-           (double)__bfloat162float(__ushort_as_bfloat16(c));
+    return (double)b_val(a) * (1.0 / 256.0) + (double)b_val(b) * (1.0 / 65536.0) +
+           (double)b_val(c) * (1.0 / 16777216.0);
   }
 }
+
+// Weights of the accumulator groups: S = w0 acc0 + w1 acc1 + w2 acc2.
+//   FP16x2: acc0 = sum hi hi, acc1 = sum (hi lo + lo hi)
+//   BF16x3: acc0 = sum hi hi, acc1 = sum (hi mid + mid hi),
+//           acc2 = sum (hi lo + lo hi + mid mid)
+template <int F>
+struct SliceWeights;
+template <>
+struct SliceWeights<kFP16x2> {
+  static constexpr float w0 = 1.0f / 4194304.0f;        // 2^-22
+  static constexpr float w1 = 1.0f / 8589934592.0f;     // 2^-33
+  static constexpr float w2 = 0.0f;
+  static constexpr int groups = 2;
+};
+template <>
+struct SliceWeights<kBF16x3> {
+  static constexpr float w0 = 1.0f / 65536.0f;          // 2^-16
+  static constexpr float w1 = 1.0f / 16777216.0f;       // 2^-24
+  static constexpr float w2 = 1.0f / 4294967296.0f;     // 2^-32
+  static constexpr int groups = 3;
+};
 
 template <int F>
 __device__ __forceinline__ void store_slices(const Slices& S, size_t idx, double x) {

@@ -1,25 +1,29 @@
 // Split-precision SP2 product step on the sm_103a tcgen05 tensor cores.
 //
 // One CTA computes one 128 x 128 upper-triangle tile (I <= J) of S = X*X for
-// the symmetric iterate X. X is held as 16-bit operand slices (FP16x2: hi, lo
-// scaled by 2^11; BF16x3: hi, mid, lo), each an ld x ld row-major matrix, so
-// both operands of tile (I, J) are K-major row panels of the same slices.
+// the symmetric iterate X. X is held as 16-bit fixed-point operand slices
+// (FP16x2: hi, lo; BF16x3: hi, mid, lo -- see sp2_slices.cuh), each an ld x ld
+// row-major matrix, so both operands of tile (I, J) are K-major row panels of
+// the same slices.
 //
 //   warp 0, one lane : TMA producer -- 128 x 64 slice boxes (128 B rows,
 //                      128 B swizzle) of the I and J row panels into a
 //                      STAGES-deep shared-memory ring (mbarrier complete_tx)
 //   warp 1, one lane : MMA issuer -- tcgen05.mma kind::f16, M = N = 128,
-//                      K = 16, FP32 accumulators in tensor memory:
-//                      acc0 += hi*hi^T, acc1 += the cross products
-//                      (FP16x2: hi*lo^T + lo*hi^T; BF16x3: hi*mid^T + mid*hi^T
-//                      + hi*lo^T + lo*hi^T + mid*mid^T); tcgen05.commit frees a
-//                      stage and finally signals the epilogue
+//                      K = 16, one FP32 accumulator in tensor memory per
+//                      weight group of the fixed-point slices: acc0 += hi*hi^T
+//                      (exact integer sums), acc1 += hi*lo^T + lo*hi^T
+//                      (FP16x2) or hi*mid^T + mid*hi^T (BF16x3), acc2 +=
+//                      hi*lo^T + lo*hi^T + mid*mid^T (BF16x3); tcgen05.commit
+//                      frees a stage and finally signals the epilogue
 //   all 4 warps      : epilogue -- tcgen05.ld of the lane (row) each thread
-//                      owns, S = acc0 + scale * acc1, the SP2 branch of §IV.A
+//                      owns, S = w0 acc0 + w1 acc1 (+ w2 acc2) in FP32 (no FP64
+//                      arithmetic: it is slow on this part), the SP2 branch of §IV.A
 //                      chosen on the device (X' = S or 2X - S), the new slices
 //                      of X' at (r, c) and at the mirror (c, r), FP64 X' when
 //                      the precision schedule may leave the split phase next,
-//                      and FP64 partial traces Tr X', ||X'||_F^2.
+//                      and the partial traces Tr X', ||X'||_F^2 (FP32 over 32
+//                      columns, folded into FP64 per chunk).
 //
 // Every mbarrier wait is bounded; a wait that runs out records
 // PROGRESS_ETIMEOUT in the solve state, stops the loop and the CTA still frees
@@ -41,7 +45,7 @@ constexpr int BN = 128;
 constexpr int BK = 64;                         // 16-bit elements = 128 B rows
 constexpr int TILE_BYTES = BM * BK * 2;        // one 128 x 64 slice box (16 KB)
 constexpr int THREADS = 128;
-constexpr int TMEM_COLS = 256;                 // acc0 | acc1, 128 columns each
+
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait gives up after 2 s
 
 template <int F>
@@ -50,6 +54,8 @@ struct Cfg {
   static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;            // A and B boxes
   static constexpr int STAGES = (F == kFP16x2) ? 3 : 2;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;    // + align + barriers
+  static constexpr int GROUPS = SliceWeights<F>::groups;             // accumulators
+  static constexpr int TMEM_COLS = (F == kFP16x2) ? 256 : 512;       // 128 columns each
 };
 
 struct TensorMaps {
@@ -284,7 +290,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), TMEM_COLS);
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), C::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       // MMA issuer
       constexpr uint32_t idesc = idesc_f16(F == kBF16x3 ? 1 : 0, BM, BN);
-      const uint32_t acc0 = tmem, acc1 = tmem + 128;
+      const uint32_t acc0 = tmem, acc1 = tmem + 128, acc2 = tmem + 256;
       bool ok = true;
       for (int kb = 0; kb < KB && ok; ++kb) {
         const int s = kb % C::STAGES;
@@ -336,13 +342,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int kk = 0; kk < BK / 16; ++kk) {
           const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 32 B per K = 16 step
           const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+          // leading group (exact integer sums), then the correction groups
           mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, first);
           mma_f16(acc1, a[0] + adv, b[1] + adv, idesc, first);
           mma_f16(acc1, a[1] + adv, b[0] + adv, idesc, 1u);
           if (F == kBF16x3) {
-            mma_f16(acc1, a[0] + adv, b[2] + adv, idesc, 1u);
-            mma_f16(acc1, a[2] + adv, b[0] + adv, idesc, 1u);
-            mma_f16(acc1, a[1] + adv, b[1] + adv, idesc, 1u);
+            mma_f16(acc2, a[0] + adv, b[2] + adv, idesc, first);
+            mma_f16(acc2, a[2] + adv, b[0] + adv, idesc, 1u);
+            mma_f16(acc2, a[1] + adv, b[1] + adv, idesc, 1u);
           }
         }
         mma_commit(empty_bar(s));  // frees the stage once these MMAs have read it
@@ -360,8 +367,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_after();
   double tr = 0.0, fr = 0.0;
   if (ok && *err == 0) {
+    using W = SliceWeights<F>;
     const int r = row_a + threadIdx.x;
-    const float scale = (F == kFP16x2) ? kLoUnscale : 1.0f;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
     const uint16_t* xs0 = buf.sl[src][0];
     const uint16_t* xs1 = buf.sl[src][1];
@@ -375,11 +382,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       tmem_ld32(lane_addr + ch * 32, v0);
       tmem_ld32(lane_addr + 128 + ch * 32, v1);
       tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v0[j] = v0[j] * W::w0 + v1[j] * W::w1;
+      if (F == kBF16x3) {
+        tmem_ld32(lane_addr + 256 + ch * 32, v1);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v0[j] += v1[j] * W::w2;
+      }
       const int c0 = row_b + ch * 32;
+      float trf = 0.0f, frf = 0.0f;  // chunk partials (FP32), folded into FP64 below
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int c = c0 + j;
-        float x = v0[j] + v1[j] * scale;
+        float x = v0[j];
         if (bit) {
           const size_t m = (size_t)c * ld + r;  // X is symmetric: read the mirror (coalesced)
           const float xo =
@@ -388,12 +404,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         v0[j] = x;
         if (r <= c) {
-          const double xd = (double)x;
           if (r == c) {
-            tr += xd;
-            fr += xd * xd;
+            trf += x;
+            frf += x * x;
           } else {
-            fr += 2.0 * xd * xd;
+            frf += 2.0f * x * x;
             // mirror (c, r): consecutive threads write consecutive r
             const size_t m = (size_t)c * ld + r;
             uint16_t a, b2, c2;
@@ -401,10 +416,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             out[0][m] = a;
             out[1][m] = b2;
             if (F == kBF16x3) out[2][m] = c2;
-            if (want_fp64) out64[m] = xd;
+            if (want_fp64) out64[m] = (double)x;
           }
         }
       }
+      tr += (double)trf;
+      fr += (double)frf;
       // direct (r, c0..c0+31)
       const size_t d = (size_t)r * ld + c0;
       if (!diag) {
@@ -439,7 +456,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncthreads();
   }
-  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+  if (warp == 0) tmem_dealloc(tmem, C::TMEM_COLS);
   if (*err && threadIdx.x == 0) {
     st->status = PROGRESS_ETIMEOUT;
     st->done = 1;
