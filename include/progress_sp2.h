@@ -74,7 +74,9 @@ typedef struct {
   double emin, emax;    /* spectral bounds; NaN (default) = Gershgorin estimate */
   int32_t loop_mode;    /* 0 = CUDA graph with a device-side WHILE node (default),
                            1 = maxiter plain launches that exit early once done */
-  int32_t reserved0;    /* must be zero */
+  int32_t slice_fixed;  /* split operand encoding: 0 = floating-point hi/lo slices
+                           (default), 1 = fixed-point slices (exact FP32 accumulation
+                           of the leading hi*hi group; absolute, not relative, precision) */
   void* loop_events[2]; /* optional cudaEvent_t pair (or NULL) recorded on the stream
                            right before and right after the product loop, so a
                            caller can time the products alone */

@@ -63,7 +63,7 @@ def gershgorin_bounds(H, out=None, stream=None):
 
 
 def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None, emax=None,
-              loop_mode=0, loop_events=None):
+              loop_mode=0, loop_events=None, slice_fixed=0):
     o = Opts()
     load().progress_opts_default(ctypes.byref(o))
     o.prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
@@ -73,6 +73,7 @@ def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None
     o.emin = math.nan if emin is None else float(emin)
     o.emax = math.nan if emax is None else float(emax)
     o.loop_mode = int(loop_mode)
+    o.slice_fixed = int(slice_fixed)
     if loop_events is not None:
         # torch.cuda.Event pair, already created (recorded once)
         o.loop_events[0] = loop_events[0].cuda_event

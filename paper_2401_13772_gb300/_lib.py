@@ -25,7 +25,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("rule", ctypes.c_int32),
                 ("fp64_prefix", ctypes.c_int32), ("maxiter", ctypes.c_int32),
                 ("emin", ctypes.c_double), ("emax", ctypes.c_double),
-                ("loop_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("loop_mode", ctypes.c_int32), ("slice_fixed", ctypes.c_int32),
                 ("loop_events", ctypes.c_void_p * 2), ("reserved", ctypes.c_int32 * 4)]
 
 

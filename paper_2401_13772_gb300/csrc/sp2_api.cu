@@ -152,8 +152,10 @@ progress_status_t ensure_buffers(Workspace* w, int ld, bool need_x64, int nslice
 
 bool is_mixed(int prec) { return prec == PROGRESS_MIXED_FP16 || prec == PROGRESS_MIXED_BF16; }
 
-int slice_fmt_of(int prec) {
-  return prec == PROGRESS_MIXED_BF16 ? sp2::kBF16x3 : sp2::kFP16x2;
+int slice_fmt_of(int prec, int fixed) {
+  const bool bf16 = prec == PROGRESS_MIXED_BF16;
+  if (fixed) return bf16 ? sp2::kBF16x3F : sp2::kFP16x2F;
+  return bf16 ? sp2::kBF16x3 : sp2::kFP16x2;
 }
 
 // Queue the product steps of one loop iteration on `s`.
@@ -308,6 +310,7 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
     return fail(PROGRESS_EINVAL, "maxiter must be in [0, 250]");
   if (o.fp64_prefix < 0) return fail(PROGRESS_EINVAL, "fp64_prefix must be >= 0");
   if (o.loop_mode != 0 && o.loop_mode != 1) return fail(PROGRESS_EINVAL, "loop_mode must be 0 or 1");
+  if (o.slice_fixed != 0 && o.slice_fixed != 1) return fail(PROGRESS_EINVAL, "slice_fixed must be 0 or 1");
   if (!isnan(o.emin) || !isnan(o.emax)) {
     if (isnan(o.emin) || isnan(o.emax) || !(o.emax > o.emin))
       return fail(PROGRESS_EINVAL, "bounds override needs emin < emax (both set)");
@@ -331,8 +334,8 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   if (st != PROGRESS_OK) return st;
   const int ld = round_up(n, 128);
   const bool need_x64 = o.prec != PROGRESS_FP32_SPLIT;
-  const int fmt = slice_fmt_of(o.prec);
-  const int nslices = o.prec == PROGRESS_FP64 ? 0 : (fmt == sp2::kBF16x3 ? 3 : 2);
+  const int fmt = slice_fmt_of(o.prec, o.slice_fixed);
+  const int nslices = o.prec == PROGRESS_FP64 ? 0 : sp2::fmt_slices(fmt);
   st = ensure_buffers(w, ld, need_x64, nslices);
   if (st != PROGRESS_OK) return st;
 

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kEwThreads) finalize_kernel(const State* __res
       if (from64) {
         v = X[src];
       } else {
-        v = join_value_d<F>(s0[src], s1[src], F == kBF16x3 ? s2[src] : (uint16_t)0);
+        v = join_value_d<F>(s0[src], s1[src], fmt_bf16(F) ? s2[src] : (uint16_t)0);
       }
       D[r * n + c] = v;
     }
@@ -205,12 +205,20 @@ cudaError_t launch_x0(const double* H, const DevBuffers& b, const SolveParams& p
   if (blocks > b.max_partials) blocks = b.max_partials;
   Slices S;
   for (int i = 0; i < 3; ++i) S.s[i] = b.sl[0][i];
-  if (p.slice_fmt == kBF16x3)
-    x0_kernel<kBF16x3><<<blocks, kEwThreads, 0, s>>>(H, b.st, b.x64[0], S, write_fp64,
-                                                     write_slices, b.partials);
-  else
-    x0_kernel<kFP16x2><<<blocks, kEwThreads, 0, s>>>(H, b.st, b.x64[0], S, write_fp64,
-                                                     write_slices, b.partials);
+  switch (p.slice_fmt) {
+#define SP2_X0(F)                                                                         \
+  case F:                                                                                 \
+    x0_kernel<F><<<blocks, kEwThreads, 0, s>>>(H, b.st, b.x64[0], S, write_fp64, write_slices, \
+                                               b.partials);                              \
+    break;
+    SP2_X0(kFP16x2)
+    SP2_X0(kBF16x3)
+    SP2_X0(kFP16x2F)
+    SP2_X0(kBF16x3F)
+#undef SP2_X0
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -218,10 +226,19 @@ cudaError_t launch_finalize(const DevBuffers& b, double* D, int64_t n, int ld, i
                             cudaStream_t s) {
   (void)ld;
   const int blocks = ew_blocks(n);
-  if (slice_fmt == kBF16x3)
-    finalize_kernel<kBF16x3><<<blocks, kEwThreads, 0, s>>>(b.st, b, D, n);
-  else
-    finalize_kernel<kFP16x2><<<blocks, kEwThreads, 0, s>>>(b.st, b, D, n);
+  switch (slice_fmt) {
+#define SP2_FIN(F)                                                    \
+  case F:                                                             \
+    finalize_kernel<F><<<blocks, kEwThreads, 0, s>>>(b.st, b, D, n); \
+    break;
+    SP2_FIN(kFP16x2)
+    SP2_FIN(kBF16x3)
+    SP2_FIN(kFP16x2F)
+    SP2_FIN(kBF16x3F)
+#undef SP2_FIN
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

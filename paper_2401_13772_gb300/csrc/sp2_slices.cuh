@@ -30,7 +30,13 @@
 
 namespace sp2 {
 
-enum SliceFmt : int { kFP16x2 = 0, kBF16x3 = 1 };
+// kFP16x2 / kBF16x3: floating-point splits (every entry keeps 22 / 24
+// significant bits relative to its own magnitude); kFP16x2F / kBF16x3F: the
+// fixed-point variants described above.
+enum SliceFmt : int { kFP16x2 = 0, kBF16x3 = 1, kFP16x2F = 2, kBF16x3F = 3 };
+
+__host__ __device__ constexpr bool fmt_bf16(int f) { return f == kBF16x3 || f == kBF16x3F; }
+__host__ __device__ constexpr int fmt_slices(int f) { return fmt_bf16(f) ? 3 : 2; }
 
 struct Slices {
   uint16_t* s[3];  // hi, lo (FP16x2) or hi, mid, lo (BF16x3); row-major, leading dim ld
@@ -47,10 +53,22 @@ __device__ __forceinline__ float b_val(uint16_t u) {
 template <int F>
 __device__ __forceinline__ void split_value_f(float x, uint16_t& a, uint16_t& b, uint16_t& c) {
   if (F == kFP16x2) {
+    const __half h = __float2half_rn(x);
+    a = h_bits(h);
+    b = h_bits(__float2half_rn((x - __half2float(h)) * 2048.0f));
+    c = 0;
+  } else if (F == kBF16x3) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    a = b_bits(h);
+    b = b_bits(m);
+    c = b_bits(__float2bfloat16_rn(r1 - __bfloat162float(m)));
+  } else if (F == kFP16x2F) {
     const float y = x * 2048.0f;  // exact scaling
     const float h = rintf(y);
-    a = h_bits(__float2half_rn(h));                        // integer, exact
-    b = h_bits(__float2half_rn((y - h) * 2048.0f));        // y - h exact (Sterbenz range)
+    a = h_bits(__float2half_rn(h));                  // integer, exact
+    b = h_bits(__float2half_rn((y - h) * 2048.0f));  // y - h is exact
     c = 0;
   } else {
     const float y = x * 256.0f;
@@ -66,6 +84,18 @@ __device__ __forceinline__ void split_value_f(float x, uint16_t& a, uint16_t& b,
 template <int F>
 __device__ __forceinline__ void split_value(double x, uint16_t& a, uint16_t& b, uint16_t& c) {
   if (F == kFP16x2) {
+    const __half h = __double2half(x);
+    a = h_bits(h);
+    b = h_bits(__double2half((x - (double)__half2float(h)) * 2048.0));
+    c = 0;
+  } else if (F == kBF16x3) {
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    const double r1 = x - (double)__bfloat162float(h);
+    const __nv_bfloat16 m = __double2bfloat16(r1);
+    a = b_bits(h);
+    b = b_bits(m);
+    c = b_bits(__double2bfloat16(r1 - (double)__bfloat162float(m)));
+  } else if (F == kFP16x2F) {
     const double y = x * 2048.0;
     const double h = rint(y);
     a = h_bits(__double2half(h));
@@ -86,6 +116,10 @@ __device__ __forceinline__ void split_value(double x, uint16_t& a, uint16_t& b, 
 template <int F>
 __device__ __forceinline__ float join_value(uint16_t a, uint16_t b, uint16_t c) {
   if (F == kFP16x2) {
+    return h_val(a) + h_val(b) * (1.0f / 2048.0f);
+  } else if (F == kBF16x3) {
+    return b_val(a) + (b_val(b) + b_val(c));
+  } else if (F == kFP16x2F) {
     return h_val(a) * (1.0f / 2048.0f) + h_val(b) * (1.0f / 4194304.0f);
   } else {
     return b_val(a) * (1.0f / 256.0f) +
@@ -96,6 +130,10 @@ __device__ __forceinline__ float join_value(uint16_t a, uint16_t b, uint16_t c) 
 template <int F>
 __device__ __forceinline__ double join_value_d(uint16_t a, uint16_t b, uint16_t c) {
   if (F == kFP16x2) {
+    return (double)h_val(a) + (double)h_val(b) * (1.0 / 2048.0);
+  } else if (F == kBF16x3) {
+    return (double)b_val(a) + (double)b_val(b) + (double)b_val(c);
+  } else if (F == kFP16x2F) {
     return (double)h_val(a) * (1.0 / 2048.0) + (double)h_val(b) * (1.0 / 4194304.0);
   } else {
     return (double)b_val(a) * (1.0 / 256.0) + (double)b_val(b) * (1.0 / 65536.0) +
@@ -104,20 +142,32 @@ __device__ __forceinline__ double join_value_d(uint16_t a, uint16_t b, uint16_t 
 }
 
 // Weights of the accumulator groups: S = w0 acc0 + w1 acc1 + w2 acc2.
-//   FP16x2: acc0 = sum hi hi, acc1 = sum (hi lo + lo hi)
-//   BF16x3: acc0 = sum hi hi, acc1 = sum (hi mid + mid hi),
-//           acc2 = sum (hi lo + lo hi + mid mid)
+//   *x2: acc0 = sum hi hi, acc1 = sum (hi lo + lo hi)
+//   *x3: acc0 = sum hi hi, acc1 = sum (hi mid + mid hi),
+//        acc2 = sum (hi lo + lo hi + mid mid)
 template <int F>
 struct SliceWeights;
 template <>
 struct SliceWeights<kFP16x2> {
+  static constexpr float w0 = 1.0f;
+  static constexpr float w1 = 1.0f / 2048.0f;
+  static constexpr float w2 = 0.0f;
+  static constexpr int groups = 2;
+};
+template <>
+struct SliceWeights<kBF16x3> {
+  static constexpr float w0 = 1.0f, w1 = 1.0f, w2 = 1.0f;
+  static constexpr int groups = 3;
+};
+template <>
+struct SliceWeights<kFP16x2F> {
   static constexpr float w0 = 1.0f / 4194304.0f;        // 2^-22
   static constexpr float w1 = 1.0f / 8589934592.0f;     // 2^-33
   static constexpr float w2 = 0.0f;
   static constexpr int groups = 2;
 };
 template <>
-struct SliceWeights<kBF16x3> {
+struct SliceWeights<kBF16x3F> {
   static constexpr float w0 = 1.0f / 65536.0f;          // 2^-16
   static constexpr float w1 = 1.0f / 16777216.0f;       // 2^-24
   static constexpr float w2 = 1.0f / 4294967296.0f;     // 2^-32
@@ -130,7 +180,7 @@ __device__ __forceinline__ void store_slices(const Slices& S, size_t idx, double
   split_value<F>(x, a, b, c);
   S.s[0][idx] = a;
   S.s[1][idx] = b;
-  if (F == kBF16x3) S.s[2][idx] = c;
+  if (fmt_bf16(F)) S.s[2][idx] = c;
 }
 
 }  // namespace sp2

@@ -207,14 +207,20 @@ cudaError_t launch_square_fp64(const DevBuffers& b, int ld, int slice_fmt,
   const int tiles = fp64_tile_count(ld);
   if (tiles > b.max_partials || ld % BM) return cudaErrorInvalidValue;
   const int smem = (int)sizeof(Smem);
-  if (slice_fmt == kBF16x3) {
-    cudaFuncSetAttribute(square_fp64_kernel<kBF16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem);
-    square_fp64_kernel<kBF16x3><<<tiles, THREADS, smem, s>>>(b, cond_handle);
-  } else {
-    cudaFuncSetAttribute(square_fp64_kernel<kFP16x2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem);
-    square_fp64_kernel<kFP16x2><<<tiles, THREADS, smem, s>>>(b, cond_handle);
+  switch (slice_fmt) {
+#define SP2_SQ64(F)                                                                        \
+  case F:                                                                                  \
+    cudaFuncSetAttribute(square_fp64_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                         smem);                                                            \
+    square_fp64_kernel<F><<<tiles, THREADS, smem, s>>>(b, cond_handle);                    \
+    break;
+    SP2_SQ64(kFP16x2)
+    SP2_SQ64(kBF16x3)
+    SP2_SQ64(kFP16x2F)
+    SP2_SQ64(kBF16x3F)
+#undef SP2_SQ64
+    default:
+      return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

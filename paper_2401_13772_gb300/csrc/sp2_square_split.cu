@@ -50,12 +50,12 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait gives up after 2 s
 
 template <int F>
 struct Cfg {
-  static constexpr int NS = (F == kFP16x2) ? 2 : 3;                 // slices
+  static constexpr int NS = fmt_slices(F);                          // slices
   static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;            // A and B boxes
-  static constexpr int STAGES = (F == kFP16x2) ? 3 : 2;
+  static constexpr int STAGES = fmt_bf16(F) ? 2 : 3;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;    // + align + barriers
   static constexpr int GROUPS = SliceWeights<F>::groups;             // accumulators
-  static constexpr int TMEM_COLS = (F == kFP16x2) ? 256 : 512;       // 128 columns each
+  static constexpr int TMEM_COLS = fmt_bf16(F) ? 512 : 256;         // 128 columns each
 };
 
 struct TensorMaps {
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer
-      constexpr uint32_t idesc = idesc_f16(F == kBF16x3 ? 1 : 0, BM, BN);
+      constexpr uint32_t idesc = idesc_f16(fmt_bf16(F) ? 1 : 0, BM, BN);
       const uint32_t acc0 = tmem, acc1 = tmem + 128, acc2 = tmem + 256;
       bool ok = true;
       for (int kb = 0; kb < KB && ok; ++kb) {
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, first);
           mma_f16(acc1, a[0] + adv, b[1] + adv, idesc, first);
           mma_f16(acc1, a[1] + adv, b[0] + adv, idesc, 1u);
-          if (F == kBF16x3) {
+          if (fmt_bf16(F)) {
             mma_f16(acc2, a[0] + adv, b[2] + adv, idesc, first);
             mma_f16(acc2, a[2] + adv, b[0] + adv, idesc, 1u);
             mma_f16(acc2, a[1] + adv, b[1] + adv, idesc, 1u);
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       tmem_ld_wait();
 #pragma unroll
       for (int j = 0; j < 32; ++j) v0[j] = v0[j] * W::w0 + v1[j] * W::w1;
-      if (F == kBF16x3) {
+      if (fmt_bf16(F)) {
         tmem_ld32(lane_addr + 256 + ch * 32, v1);
         tmem_ld_wait();
 #pragma unroll
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (bit) {
           const size_t m = (size_t)c * ld + r;  // X is symmetric: read the mirror (coalesced)
           const float xo =
-              join_value<F>(xs0[m], xs1[m], F == kBF16x3 ? xs2[m] : (uint16_t)0);
+              join_value<F>(xs0[m], xs1[m], fmt_bf16(F) ? xs2[m] : (uint16_t)0);
           x = 2.0f * xo - x;
         }
         v0[j] = x;
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             split_value_f<F>(x, a, b2, c2);
             out[0][m] = a;
             out[1][m] = b2;
-            if (F == kBF16x3) out[2][m] = c2;
+            if (fmt_bf16(F)) out[2][m] = c2;
             if (want_fp64) out64[m] = (double)x;
           }
         }
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             split_value_f<F>(v0[j], a, b2, c2);
             out[0][d + j] = a;
             out[1][d + j] = b2;
-            if (F == kBF16x3) out[2][d + j] = c2;
+            if (fmt_bf16(F)) out[2][d + j] = c2;
             if (want_fp64) out64[d + j] = (double)v0[j];
           }
         }
@@ -503,7 +503,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
 bool encode_maps(const DevBuffers& b, int ld, int fmt, TensorMaps* maps) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encoder();
   if (!enc) return false;
-  const int ns = (fmt == kFP16x2) ? 2 : 3;
+  const int ns = fmt_slices(fmt);
   memset(maps, 0, sizeof *maps);
   for (int k = 0; k < 2; ++k) {
     for (int j = 0; j < ns; ++j) {
@@ -513,8 +513,8 @@ bool encode_maps(const DevBuffers& b, int ld, int fmt, TensorMaps* maps) {
       cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
       cuuint32_t estr[2] = {1, 1};
       CUresult r = enc(&maps->m[k][j],
-                       fmt == kFP16x2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                       fmt_bf16(fmt) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                        2, (void*)b.sl[k][j], dims, strides, box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -544,16 +544,22 @@ cudaError_t launch_square_split(const DevBuffers& b, const SolveParams& p,
   if (tiles > b.max_partials) return cudaErrorInvalidValue;
   TensorMaps maps;
   if (!encode_maps(b, ld, p.slice_fmt, &maps)) return cudaErrorInvalidValue;
-  if (p.slice_fmt == kBF16x3) {
-    const int smem = Cfg<kBF16x3>::SMEM;
-    cudaFuncSetAttribute(square_split_kernel<kBF16x3>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    square_split_kernel<kBF16x3><<<tiles, THREADS, smem, s>>>(maps, b, cond_handle);
-  } else {
-    const int smem = Cfg<kFP16x2>::SMEM;
-    cudaFuncSetAttribute(square_split_kernel<kFP16x2>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    square_split_kernel<kFP16x2><<<tiles, THREADS, smem, s>>>(maps, b, cond_handle);
+  switch (p.slice_fmt) {
+#define SP2_SQS(F)                                                                     \
+  case F: {                                                                            \
+    const int smem = Cfg<F>::SMEM;                                                     \
+    cudaFuncSetAttribute(square_split_kernel<F>,                                       \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);           \
+    square_split_kernel<F><<<tiles, THREADS, smem, s>>>(maps, b, cond_handle);         \
+    break;                                                                             \
+  }
+    SP2_SQS(kFP16x2)
+    SP2_SQS(kBF16x3)
+    SP2_SQS(kFP16x2F)
+    SP2_SQS(kBF16x3F)
+#undef SP2_SQS
+    default:
+      return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
