@@ -10,20 +10,27 @@
 //                      128 B swizzle) of the I and J row panels into a
 //                      STAGES-deep shared-memory ring (mbarrier complete_tx)
 //   warp 1, one lane : MMA issuer -- tcgen05.mma kind::f16, M = N = 128,
-//                      K = 16, one FP32 accumulator in tensor memory per
-//                      weight group of the fixed-point slices: acc0 += hi*hi^T
-//                      (exact integer sums), acc1 += hi*lo^T + lo*hi^T
-//                      (FP16x2) or hi*mid^T + mid*hi^T (BF16x3), acc2 +=
-//                      hi*lo^T + lo*hi^T + mid*mid^T (BF16x3); tcgen05.commit
-//                      frees a stage and finally signals the epilogue
-//   all 4 warps      : epilogue -- tcgen05.ld of the lane (row) each thread
-//                      owns, S = w0 acc0 + w1 acc1 (+ w2 acc2) in FP32 (no FP64
-//                      arithmetic: it is slow on this part), the SP2 branch of §IV.A
-//                      chosen on the device (X' = S or 2X - S), the new slices
-//                      of X' at (r, c) and at the mirror (c, r), FP64 X' when
-//                      the precision schedule may leave the split phase next,
-//                      and the partial traces Tr X', ||X'||_F^2 (FP32 over 32
-//                      columns, folded into FP64 per chunk).
+//                      K = 16, FP32 accumulators in tensor memory, one per
+//                      weight group of the slices: acc0 += hi*hi^T,
+//                      acc1 += hi*lo^T + lo*hi^T (x2) or hi*mid^T + mid*hi^T
+//                      (x3), acc2 += hi*lo^T + lo*hi^T + mid*mid^T (x3).
+//                      The leading group acc0 alternates between two chunk
+//                      buffers of CHUNK k-blocks (K = 256): the tensor core's
+//                      FP32 accumulation truncates, and over a whole K = n
+//                      chain of same-sign products (the diagonal of X*X) that
+//                      truncation becomes a measurable bias; short chains
+//                      summed with round-to-nearest adds remove it.
+//   warps 4..7       : drain -- each thread owns one tensor-memory lane (a
+//                      tile row); it adds every finished acc0 chunk into 128
+//                      FP32 registers and frees the buffer (mbarrier), then
+//                      runs the epilogue: S = w0 sum0 + w1 acc1 (+ w2 acc2)
+//                      in FP32 (no FP64 arithmetic: it is slow on this part),
+//                      the SP2 branch of §IV.A chosen on the device (X' = S or
+//                      2X - S), the new slices of X' at (r, c) and at the
+//                      mirror (c, r), FP64 X' when the precision schedule may
+//                      leave the split phase next, and the partial traces
+//                      Tr X', ||X'||_F^2 (FP32 over 32 columns, folded into
+//                      FP64 per chunk).
 //
 // Every mbarrier wait is bounded; a wait that runs out records
 // PROGRESS_ETIMEOUT in the solve state, stops the loop and the CTA still frees
@@ -44,7 +51,10 @@ constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 64;                         // 16-bit elements = 128 B rows
 constexpr int TILE_BYTES = BM * BK * 2;        // one 128 x 64 slice box (16 KB)
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;       // warp 0 TMA, warp 1 MMA, warps 4..7 drain + epilogue
+constexpr int DRAIN_WARPS = 4;     // one per 32-lane quarter of tensor memory
+constexpr int CHUNK = 4;           // k-blocks per leading-group accumulation chunk
+constexpr int TMEM_COLS = 512;     // acc0 x2 | acc1 | acc2, 128 columns each
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait gives up after 2 s
 
@@ -54,8 +64,6 @@ struct Cfg {
   static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;            // A and B boxes
   static constexpr int STAGES = fmt_bf16(F) ? 2 : 3;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;    // + align + barriers
-  static constexpr int GROUPS = SliceWeights<F>::groups;             // accumulators
-  static constexpr int TMEM_COLS = fmt_bf16(F) ? 512 : 256;         // 128 columns each
 };
 
 struct TensorMaps {
@@ -279,6 +287,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   auto empty_bar = [&](int s) { return bars + 8u * (C::STAGES + s); };
   const uint32_t accum_bar = bars + 8u * (2 * C::STAGES);
 
+  const uint32_t chunk_full = bars + 8u * (2 * C::STAGES + 1);   // [2]
+  const uint32_t chunk_empty = bars + 8u * (2 * C::STAGES + 3);  // [2]
+
   if (threadIdx.x == 0) {
     s_err = 0;
     s_consumed = 0;
@@ -287,10 +298,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(empty_bar(s), 1);
     }
     mbar_init(accum_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(chunk_full + 8u * b, 1);
+      mbar_init(chunk_empty + 8u * b, DRAIN_WARPS);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), C::TMEM_COLS);
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -298,6 +313,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int* err = &s_err;
 
   const int KB = ld / BK;
+  const int NC = (KB + CHUNK - 1) / CHUNK;  // leading-group chunks
   int issued = 0;  // k-blocks whose loads were issued (producer thread)
   if (warp == 0) {
     if (lane == 0) {
@@ -319,11 +335,24 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer
+      // MMA issuer. The leading group goes to one of two chunk accumulators
+      // (CHUNK k-blocks each) that the drain warps empty in turn; the
+      // correction groups accumulate over the whole K.
       constexpr uint32_t idesc = idesc_f16(fmt_bf16(F) ? 1 : 0, BM, BN);
-      const uint32_t acc0 = tmem, acc1 = tmem + 128, acc2 = tmem + 256;
+      const uint32_t acc1 = tmem + 256, acc2 = tmem + 384;
       bool ok = true;
       for (int kb = 0; kb < KB && ok; ++kb) {
+        const int c = kb / CHUNK, cb = c & 1;
+        const bool chunk_first = (kb % CHUNK) == 0;
+        const bool chunk_last = (kb % CHUNK) == CHUNK - 1 || kb == KB - 1;
+        const uint32_t acc0 = tmem + 128u * cb;
+        if (chunk_first) {
+          if (!mbar_wait(chunk_empty + 8u * cb, ((uint32_t)(c >> 1) & 1u) ^ 1u, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
         const int s = kb % C::STAGES;
         const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
         if (!mbar_wait(full_bar(s), ph, err)) {
@@ -342,8 +371,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int kk = 0; kk < BK / 16; ++kk) {
           const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 32 B per K = 16 step
           const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-          // leading group (exact integer sums), then the correction groups
-          mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, first);
+          const uint32_t chunk_acc = (chunk_first && kk == 0) ? 0u : 1u;
+          mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, chunk_acc);
           mma_f16(acc1, a[0] + adv, b[1] + adv, idesc, first);
           mma_f16(acc1, a[1] + adv, b[0] + adv, idesc, 1u);
           if (fmt_bf16(F)) {
@@ -353,6 +382,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
         mma_commit(empty_bar(s));  // frees the stage once these MMAs have read it
+        if (chunk_last) mma_commit(chunk_full + 8u * cb);
         s_consumed = kb + 1;
       }
       mma_commit(accum_bar);  // all MMAs issued so far are complete -> epilogue
@@ -360,32 +390,57 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
   }
 
-  // ---- epilogue: every thread owns TMEM lane = tile row threadIdx.x
+  // ---- drain warps: thread owns TMEM lane = tile row, sums the leading-group
+  // chunks with round-to-nearest FP32 adds, then runs the epilogue.
+  const bool drain = warp >= THREADS / 32 - DRAIN_WARPS;
+  const int row = threadIdx.x - (THREADS - 128);
+  const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  float sum0[BN];
+#pragma unroll
+  for (int j = 0; j < BN; ++j) sum0[j] = 0.0f;
+  if (drain) {
+    for (int c = 0; c < NC; ++c) {
+      const int cb = c & 1;
+      if (!mbar_wait(chunk_full + 8u * cb, (uint32_t)(c >> 1) & 1u, err)) break;
+      tc_fence_after();
+#pragma unroll
+      for (int q = 0; q < BN / 32; ++q) {
+        float v[32];
+        tmem_ld32(lane_addr + 128u * cb + q * 32, v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sum0[q * 32 + j] += v[j];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(chunk_empty + 8u * cb)
+                     : "memory");
+    }
+  }
   // (the MMA thread always commits accum_bar, so this wait does not abort
   // early: no MMA may still be writing tensor memory past it)
   const bool ok = mbar_wait(accum_bar, 0u, err, false);
   tc_fence_after();
   double tr = 0.0, fr = 0.0;
-  if (ok && *err == 0) {
+  if (drain && ok && *err == 0) {
     using W = SliceWeights<F>;
-    const int r = row_a + threadIdx.x;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const int r = row_a + row;
     const uint16_t* xs0 = buf.sl[src][0];
     const uint16_t* xs1 = buf.sl[src][1];
     const uint16_t* xs2 = buf.sl[src][2];
     uint16_t* out[3] = {buf.sl[dst][0], buf.sl[dst][1], buf.sl[dst][2]};
     double* out64 = buf.x64[dst];
     const bool diag = (I == J);
-#pragma unroll 1
+#pragma unroll
     for (int ch = 0; ch < BN / 32; ++ch) {
       float v0[32], v1[32];
-      tmem_ld32(lane_addr + ch * 32, v0);
-      tmem_ld32(lane_addr + 128 + ch * 32, v1);
+      tmem_ld32(lane_addr + 256 + ch * 32, v1);
       tmem_ld_wait();
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v0[j] = v0[j] * W::w0 + v1[j] * W::w1;
+      for (int j = 0; j < 32; ++j) v0[j] = sum0[ch * 32 + j] * W::w0 + v1[j] * W::w1;
       if (fmt_bf16(F)) {
-        tmem_ld32(lane_addr + 256 + ch * 32, v1);
+        tmem_ld32(lane_addr + 384 + ch * 32, v1);
         tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 32; ++j) v0[j] += v1[j] * W::w2;
@@ -456,7 +511,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncthreads();
   }
-  if (warp == 0) tmem_dealloc(tmem, C::TMEM_COLS);
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
   if (*err && threadIdx.x == 0) {
     st->status = PROGRESS_ETIMEOUT;
     st->done = 1;
