@@ -138,6 +138,17 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
 /* Synchronize `stream` and report the last solve queued on it. */
 progress_status_t progress_sp2_query(void* stream, progress_info_t* info);
 
+/*
+ * Synchronize `stream` and copy the per-iteration history of the last solve
+ * queued on it into host arrays of capacity `cap` (either may be NULL):
+ *   idem[k]   |Tr X_k^2 - Tr X_k| of iterate X_k, k = 0..iters
+ *   margin[k] signed margin of the branch rule at product k, k < iters
+ *             (nearer rule: |Tr X^2 - Nocc| - |2 Tr X - Tr X^2 - Nocc|,
+ *              paper rule: Nocc - Tr X); a positive margin selects 2X - X^2
+ * Returns the number of iterates written to idem (iters + 1, at most cap).
+ */
+int32_t progress_sp2_history(void* stream, double* idem, double* margin, int32_t cap);
+
 /* Free the cached workspace of `stream` on the current device (synchronizes it). */
 progress_status_t progress_release(void* stream);
 

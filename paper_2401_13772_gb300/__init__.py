@@ -119,6 +119,19 @@ def sp2_dense_ex(H, nocc, tol, D=None, info=True, stream=None, raise_on_status=T
     return D
 
 
+def history(stream=None, cap=256):
+    """(idem, margin) numpy arrays of the last solve on the stream: idem[k] =
+    |Tr X_k^2 - Tr X_k|, margin[k] = signed branch-rule margin of product k."""
+    import numpy as np
+    idem = np.zeros(cap)
+    margin = np.zeros(cap)
+    cnt = load().progress_sp2_history(_stream_ptr(stream), ctypes.c_void_p(idem.ctypes.data),
+                                      ctypes.c_void_p(margin.ctypes.data), cap)
+    if cnt < 0:
+        check(_lib.ECUDA)
+    return idem[:cnt], margin[:max(cnt - 1, 0)]
+
+
 def release(stream=None):
     """Free the library's cached workspace of the stream."""
     check(load().progress_release(_stream_ptr(stream)))

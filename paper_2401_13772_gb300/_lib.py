@@ -56,6 +56,7 @@ SIGNATURES = {
     "progress_sp2_dense_ex": (ctypes.c_int, [_P, _I64, _I64, _D, _P, ctypes.POINTER(Opts),
                                              ctypes.POINTER(Info), _P]),
     "progress_sp2_query": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "progress_sp2_history": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
     "progress_release": (ctypes.c_int, [_P]),
     "progress_release_all": (ctypes.c_int, []),
     "progress_last_error": (ctypes.c_char_p, []),

@@ -387,6 +387,26 @@ progress_status_t progress_sp2_query(void* stream, progress_info_t* info) {
   return query(w, info);
 }
 
+int32_t progress_sp2_history(void* stream, double* idem, double* margin, int32_t cap) {
+  Workspace* w = nullptr;
+  if (get_workspace((cudaStream_t)stream, &w) != PROGRESS_OK || cap < 0) return -1;
+  if (cudaMemcpyAsync(w->h_state, w->buf.st, sizeof(sp2::State), cudaMemcpyDeviceToHost,
+                      w->stream) != cudaSuccess ||
+      cudaStreamSynchronize(w->stream) != cudaSuccess) {
+    cuda_fail(cudaGetLastError(), "history readback");
+    return -1;
+  }
+  const sp2::State& st = *w->h_state;
+  int cnt = st.iter + 1;
+  if (cnt > sp2::kMaxHist) cnt = sp2::kMaxHist;
+  if (cnt > cap) cnt = cap;
+  for (int k = 0; k < cnt; ++k) {
+    if (idem) idem[k] = st.idem_hist[k];
+    if (margin) margin[k] = k < st.iter ? st.margin_hist[k] : 0.0;
+  }
+  return cnt;
+}
+
 progress_status_t progress_release(void* stream) {
   int dev = 0;
   CK(cudaGetDevice(&dev), "cudaGetDevice");

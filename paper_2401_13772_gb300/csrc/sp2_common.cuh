@@ -131,13 +131,18 @@ __device__ inline void decide(State* st) {
       st->split_stall = 0;
     }
     if (phase == kPhaseSplit && k > 0) {
-      // Low precision stops helping once the idempotency error reaches its
-      // round-off floor: two steps in a row without a 0.1 % improvement.
+      // Low precision stops helping once the idempotency error sits on its
+      // round-off floor. Plateaus of the error above 0.01 are not that floor:
+      // each eigenvalue still between 0.01 and 0.99 adds at least 0.0099, and
+      // SP2 holds the last few pairs around the gap near 0.5 for many steps
+      // while it separates them. So: two steps without a 0.1 % improvement
+      // below 0.01, or eight steps without one anywhere.
       if (idem < st->best_split_idem * 0.999) {
         st->best_split_idem = idem;
         st->split_stall = 0;
-      } else if (++st->split_stall >= 2 && idem < 1.0) {
-        stalled = true;
+      } else {
+        ++st->split_stall;
+        if ((st->split_stall >= 2 && idem < 0.01) || st->split_stall >= 8) stalled = true;
       }
     }
     if (stalled && st->prec != PROGRESS_FP32_SPLIT) phase = kPhaseRefine;  // MIXED
@@ -149,8 +154,8 @@ __device__ inline void decide(State* st) {
     st->done = 1;
     return;
   }
-  // Convergence is tested in FP64-accurate phases only.
-  if (phase != kPhaseSplit && idem < st->tol) {
+  // Convergence is tested in FP64-accurate phases and in the all-split mode.
+  if ((phase != kPhaseSplit || st->prec == PROGRESS_FP32_SPLIT) && idem < st->tol) {
     st->converged = 1;
     st->done = 1;
     return;
