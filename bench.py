@@ -46,12 +46,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64",
+    ap.add_argument("--prec", default="mixed_fp16",
                     choices=["fp64", "fp32_split", "mixed_fp16", "mixed_bf16"])
     ap.add_argument("--sites", type=int, default=1024)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--fp64-prefix", type=int, default=12)
+    ap.add_argument("--fp64-prefix", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -135,14 +135,15 @@ __device__ inline void decide(State* st) {
       // round-off floor. Plateaus of the error above 0.01 are not that floor:
       // each eigenvalue still between 0.01 and 0.99 adds at least 0.0099, and
       // SP2 holds the last few pairs around the gap near 0.5 for many steps
-      // while it separates them. So: two steps without a 0.1 % improvement
-      // below 0.01, or eight steps without one anywhere.
+      // while it separates them (and the first steps oscillate far above 1).
+      // So: two steps without a 0.1 % improvement below 0.01, or eight below 1.
       if (idem < st->best_split_idem * 0.999) {
         st->best_split_idem = idem;
         st->split_stall = 0;
       } else {
         ++st->split_stall;
-        if ((st->split_stall >= 2 && idem < 0.01) || st->split_stall >= 8) stalled = true;
+        if ((st->split_stall >= 2 && idem < 0.01) || (st->split_stall >= 8 && idem < 1.0))
+          stalled = true;
       }
     }
     if (stalled && st->prec != PROGRESS_FP32_SPLIT) phase = kPhaseRefine;  // MIXED
