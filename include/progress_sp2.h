@@ -135,6 +135,27 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
                                         double* dD, const progress_opts_t* opts,
                                         progress_info_t* info, void* stream);
 
+/*
+ * FP64 SP2 solve (same arithmetic and defaults as progress_sp2_dense) that
+ * allocates no memory at all. The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- code running while a
+ * stream is captured in global capture mode, where cudaMalloc is a
+ * prohibited call; applications whose memory pool already owns the whole
+ * device; and time-stepping codes (QMD calls the solver every step) that
+ * must not pay allocation latency. The caller still passes H and D.
+ *   Limit: n <= 1024; larger n returns PROGRESS_EINVAL.
+ *   Work space: one static device array of about 16.1 MiB inside the library
+ *   (every GPU that loads the library holds it until the process exits). Its
+ *   device address is looked up on the first call on each device, so make
+ *   that first call before any stream capture begins.
+ *   Every call shares that array and it keeps the previous call's contents;
+ *   the solve clears what has to start at zero. Calls whose work overlaps on
+ *   the GPU (e.g. on two streams at once) race on it: serialize them.
+ *   Asynchronous on `stream`; no status readback (no host-side state).
+ */
+progress_status_t progress_sp2_dense_noalloc(const double* dH, int64_t n, int64_t nocc,
+                                             double tol, double* dD, void* stream);
+
 /* Synchronize `stream` and report the last solve queued on it. */
 progress_status_t progress_sp2_query(void* stream, progress_info_t* info);
 

@@ -55,6 +55,7 @@ SIGNATURES = {
     "progress_sp2_dense": (ctypes.c_int, [_P, _I64, _I64, _D, _P, _P]),
     "progress_sp2_dense_ex": (ctypes.c_int, [_P, _I64, _I64, _D, _P, ctypes.POINTER(Opts),
                                              ctypes.POINTER(Info), _P]),
+    "progress_sp2_dense_noalloc": (ctypes.c_int, [_P, _I64, _I64, _D, _P, _P]),
     "progress_sp2_query": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "progress_sp2_history": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
     "progress_release": (ctypes.c_int, [_P]),

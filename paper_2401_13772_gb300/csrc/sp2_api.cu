@@ -250,6 +250,10 @@ progress_status_t query(Workspace* w, progress_info_t* info) {
 
 }  // namespace
 
+namespace sp2 {
+void set_last_error(const char* what) { g_err = what; }
+}  // namespace sp2
+
 extern "C" {
 
 void progress_opts_default(progress_opts_t* o) {

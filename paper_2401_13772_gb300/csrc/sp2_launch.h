@@ -48,6 +48,9 @@ cudaError_t launch_finalize(const DevBuffers& b, double* D, int64_t n, int ld, i
                             cudaStream_t s);
 
 int fp64_tile_count(int ld);
+
+// Record the text that progress_last_error() returns on this thread.
+void set_last_error(const char* what);
 int split_tile_count(int ld);
 
 }  // namespace sp2
