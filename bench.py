@@ -55,6 +55,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-check", action="store_true",
+                    help="skip the torch-side invariants of D (profiling runs)")
+    ap.add_argument("--loop-mode", type=int, default=0,
+                    help="0: device-driven WHILE graph; 1: plain launches (profilers)")
     return ap.parse_args()
 
 
@@ -234,14 +238,17 @@ def main():
             e.record()
         return evs
 
-    opts = dict(prec=args.prec, fp64_prefix=args.fp64_prefix)
+    opts = dict(prec=args.prec, fp64_prefix=args.fp64_prefix, loop_mode=args.loop_mode)
     # warm-up (builds the loop graph) and the iteration count
     info = None
     for _ in range(max(1, args.warmup)):
         _, info = pkg.sp2_dense_ex(H, nocc, args.tol, D=D, **opts)
     iters = info["iters"]
     body_kernels = 1 if args.prec in ("fp64", "fp32_split") else 2
-    launches_per_solve = 3 + body_kernels * max(iters, 1) + 1
+    if args.loop_mode == 0:
+        launches_per_solve = 3 + body_kernels * max(iters, 1) + 1
+    else:
+        launches_per_solve = 3 + body_kernels * (100 + 1) + 1
 
     K = args.steps
     ev_s, ev_e = mk_events(K), mk_events(K)
@@ -281,29 +288,63 @@ def main():
 
     # per-solve check of the result (status of the last timed solve)
     _, qinfo = pkg.sp2_dense_ex(H, nocc, args.tol, D=D, **opts)
-    # accuracy invariants of D (torch FP64 matmul, outside the timed region)
-    Dd = D
-    idem = float((Dd @ Dd - Dd).abs().max())
-    trace_err = abs(float(torch.trace(Dd)) - nocc)
-    comm = float((H @ Dd - Dd @ H).abs().max()) / float(H.abs().max())
+    D_main = D.clone()
+    check = {}
+    if not args.no_check:
+        # accuracy invariants of D (torch FP64 matmul, outside the timed region)
+        check = {"idempotency_max": float((D_main @ D_main - D_main).abs().max()),
+                 "trace_err": abs(float(torch.trace(D_main)) - nocc),
+                 "commutator_max_rel": float((H @ D_main - D_main @ H).abs().max()) /
+                 float(H.abs().max())}
 
-    # dominant kernel: the product step, timed as loop time / products
+    # Product-kernel launch durations. Inside the WHILE graph a launch cannot
+    # be bracketed by events, so the loop region is timed per step (events
+    # recorded by the library around the loop) and divided by the products.
+    # In the mixed modes the two kernels share that region: the split
+    # kernel's own average comes from an all-split solve of the same matrix
+    # and is subtracted.
     flops_alg = float(n) * n * (n + 1)  # one symmetric square, upper triangle
-    step_kernel_ms = statistics.mean(loop_ms) / max(iters, 1)
     peaks, peak_src = load_peaks()
-    if args.prec == "fp64":
-        peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]) * (
-            NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS)
-        peak_note = f"fp64: {peak_src} bf16 burst x nominal fp64/bf16 ratio (1.25/2250)"
+    bf16_peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
+    fp64_peak = bf16_peak * (NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS)
+    loop_mean = statistics.mean(loop_ms)
+    phases = qinfo["phase_iters"]
+    n_fp64 = phases[0] + phases[2]
+    n_split = phases[1]
+
+    def roof(kernel, ms, peak, note):
+        ach = flops_alg / (ms * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": kernel, "peak_source": note,
+                "flops_per_launch": flops_alg, "avg_launch_ms": ms}
+
+    note64 = f"fp64: {peak_src} bf16 burst x nominal fp64/bf16 ratio (1.25/2250)"
+    note16 = f"fp16/bf16 dense, {peak_src} burst"
+    split_ms = None
+    if n_split > 0:
+        if n_fp64 == 0:
+            split_ms = loop_mean / n_split
+        else:
+            sp_s, sp_e = mk_events(1)[0], mk_events(1)[0]
+            pkg.sp2_dense_ex(H, nocc, args.tol, D=D, prec="fp32_split", fp64_prefix=0,
+                             loop_mode=args.loop_mode)
+            _, sinfo = pkg.sp2_dense_ex(H, nocc, args.tol, D=D, prec="fp32_split",
+                                        loop_events=(sp_s, sp_e), loop_mode=args.loop_mode)
+            torch.cuda.synchronize()
+            split_ms = sp_s.elapsed_time(sp_e) / max(sinfo["iters"], 1)
+    fp64_ms = None
+    if n_fp64 > 0:
+        fp64_ms = (loop_mean - n_split * (split_ms or 0.0)) / n_fp64
+    if fp64_ms is not None and (split_ms is None or n_fp64 * fp64_ms >= n_split * split_ms):
+        roofline = roof("square_fp64_kernel (FP64 DMMA)", fp64_ms, fp64_peak, note64)
+        secondary = roof("square_split_kernel (tcgen05)", split_ms, bf16_peak, note16) \
+            if split_ms else None
     else:
-        peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
-        peak_note = f"fp16/bf16 dense, {peak_src} burst"
-    achieved = flops_alg / (step_kernel_ms * 1e-3) / 1e12
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "square_fp64_kernel" if args.prec == "fp64" else "square_split_kernel",
-                "peak_source": peak_note,
-                "flops_per_launch": flops_alg, "avg_launch_ms": step_kernel_ms}
+        roofline = roof("square_split_kernel (tcgen05)", split_ms, bf16_peak, note16)
+        secondary = roof("square_fp64_kernel (FP64 DMMA)", fp64_ms, fp64_peak, note64) \
+            if fp64_ms else None
+    if secondary is not None:
+        roofline["secondary"] = secondary
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -318,8 +359,7 @@ def main():
                        "l2": "flushed before each step (256 MiB write, outside events)"},
             "iters": iters, "status": qinfo["status"], "phase_iters": qinfo["phase_iters"],
             "tflops_algorithmic": iters * flops_alg / (ms_per_step * 1e-3) / 1e12,
-            "d_check": {"idempotency_max": idem, "trace_err": trace_err,
-                        "commutator_max_rel": comm},
+            "d_check": check,
             "roofline": roofline, "gpu_launches": launches_per_solve * K,
             "clocks": clk}
 
@@ -335,7 +375,9 @@ def main():
             flush.zero_()
             es[i].record(stream)
             Hd2.copy_(Hh, non_blocking=True)
-            pkg.sp2_dense(Hd2, nocc, args.tol, D=Dd2) if args.prec == "fp64" else \
+            if args.prec == "fp64" and args.loop_mode == 0:
+                pkg.sp2_dense(Hd2, nocc, args.tol, D=Dd2)
+            else:
                 pkg.sp2_dense_ex(Hd2, nocc, args.tol, D=Dd2, info=False, **opts)
             Dh.copy_(Dd2, non_blocking=True)
             ee[i].record(stream)
@@ -369,7 +411,7 @@ def main():
         t0 = time.perf_counter()
         ref = oracle.sp2_plain(H_np, nocc, args.tol)
         sec = time.perf_counter() - t0
-        err = float(np.abs(D.cpu().numpy() - ref["D"]).max())
+        err = float(np.abs(D_main.cpu().numpy() - ref["D"]).max())
         line["d_check"]["max_abs_err_vs_oracle"] = err
         line["d_check"]["gate"] = 1e-10 if args.prec == "fp64" else 1e-5
         line["d_check"]["oracle_iters"] = ref["iters"]
