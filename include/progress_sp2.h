@@ -156,6 +156,31 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
 progress_status_t progress_sp2_dense_noalloc(const double* dH, int64_t n, int64_t nocc,
                                              double tol, double* dD, void* stream);
 
+/*
+ * Batched SP2: `batch` independent dense problems of uneven size -- the parts
+ * of a graph-partitioned system, solved "independently and concurrently"
+ * (§VIII.B) -- in one persistent kernel launch (captured once in a CUDA graph
+ * and replayed while the batch layout and pointers stay the same). Each CTA
+ * takes whole instances, largest first, from a device work queue and runs
+ * their full SP2 loop itself (split FP16 hi+lo products on tcgen05 tensor
+ * cores, FP32 accumulation, FP64 traces and decisions).
+ *   h_n, h_offset, h_nocc  HOST arrays [batch]: order n_i (1..4096), element
+ *                          offset of instance i in dH/dD, occupied states
+ *   dH  device, packed FP64 inputs: instance i is n_i x n_i row-major at
+ *       dH + h_offset[i]; read only
+ *   dD  device, packed outputs with the same layout; written
+ *   d_iters, d_status  device int32 [batch] or NULL: products performed and
+ *       progress_status_t per instance (-1 if the instance was not reached)
+ *   opts  NULL or prec = PROGRESS_FP32_SPLIT (the only batched precision),
+ *         rule, maxiter; other fields ignored
+ * Asynchronous on `stream`. Errors: EINVAL (bad sizes), EUNSUPPORTED (other
+ * precisions or a GPU without tcgen05), ENOMEM, ECUDA.
+ */
+progress_status_t progress_sp2_batched(int32_t batch, const int32_t* h_n, const int64_t* h_offset,
+                                       const int32_t* h_nocc, const double* dH, double tol,
+                                       double* dD, int32_t* d_iters, int32_t* d_status,
+                                       const progress_opts_t* opts, void* stream);
+
 /* Synchronize `stream` and report the last solve queued on it. */
 progress_status_t progress_sp2_query(void* stream, progress_info_t* info);
 

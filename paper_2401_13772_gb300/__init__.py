@@ -119,6 +119,51 @@ def sp2_dense_ex(H, nocc, tol, D=None, info=True, stream=None, raise_on_status=T
     return D
 
 
+def pack_batch(mats):
+    """Pack a list of square numpy matrices into one FP64 vector.
+    Returns (packed, n, offsets) with offsets in elements."""
+    import numpy as np
+    n = np.array([m.shape[0] for m in mats], dtype=np.int32)
+    sizes = n.astype(np.int64) ** 2
+    offsets = np.zeros(len(mats), dtype=np.int64)
+    if len(mats) > 1:
+        offsets[1:] = np.cumsum(sizes)[:-1]
+    packed = np.empty(int(sizes.sum()), dtype=np.float64)
+    for m, o, sz in zip(mats, offsets, sizes):
+        packed[o:o + sz] = np.ascontiguousarray(m, dtype=np.float64).ravel()
+    return packed, n, offsets
+
+
+def sp2_batched(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", maxiter=100,
+                stream=None):
+    """Batched split-precision SP2 over packed device inputs.
+
+    H_packed: 1-D float64 CUDA tensor; n, offsets, nocc: host int sequences.
+    Returns (D_packed, iters, status) with iters/status as int32 CUDA tensors.
+    """
+    import numpy as np
+    import torch
+    if not (isinstance(H_packed, torch.Tensor) and H_packed.is_cuda and
+            H_packed.dtype == torch.float64 and H_packed.dim() == 1 and H_packed.is_contiguous()):
+        raise TypeError("H_packed must be a contiguous 1-D float64 CUDA tensor")
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    nocc = np.ascontiguousarray(nocc, dtype=np.int32)
+    b = len(n)
+    if D_packed is None:
+        D_packed = torch.empty_like(H_packed)
+    iters = torch.zeros(b, dtype=torch.int32, device=H_packed.device)
+    status = torch.zeros(b, dtype=torch.int32, device=H_packed.device)
+    o = make_opts(prec="fp32_split", rule=rule, maxiter=maxiter)
+    with torch.cuda.device(H_packed.device):
+        check(load().progress_sp2_batched(
+            b, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(offsets.ctypes.data),
+            ctypes.c_void_p(nocc.ctypes.data), ctypes.c_void_p(H_packed.data_ptr()), float(tol),
+            ctypes.c_void_p(D_packed.data_ptr()), ctypes.c_void_p(iters.data_ptr()),
+            ctypes.c_void_p(status.data_ptr()), ctypes.byref(o), _stream_ptr(stream)))
+    return D_packed, iters, status
+
+
 def history(stream=None, cap=256):
     """(idem, margin) numpy arrays of the last solve on the stream: idem[k] =
     |Tr X_k^2 - Tr X_k|, margin[k] = signed branch-rule margin of product k."""

@@ -56,6 +56,8 @@ SIGNATURES = {
     "progress_sp2_dense_ex": (ctypes.c_int, [_P, _I64, _I64, _D, _P, ctypes.POINTER(Opts),
                                              ctypes.POINTER(Info), _P]),
     "progress_sp2_dense_noalloc": (ctypes.c_int, [_P, _I64, _I64, _D, _P, _P]),
+    "progress_sp2_batched": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _D, _P, _P, _P,
+                                            ctypes.POINTER(Opts), _P]),
     "progress_sp2_query": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "progress_sp2_history": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
     "progress_release": (ctypes.c_int, [_P]),

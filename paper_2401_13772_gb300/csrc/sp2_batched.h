@@ -1,0 +1,47 @@
+// Batched SP2 solver: host/device interface (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sp2 {
+namespace batched {
+
+struct Instance {
+  int32_t n;       // matrix order
+  int32_t m;       // padded order (multiple of 128)
+  int32_t nocc;    // occupied states
+  int32_t pad;
+  int64_t row0;    // first row in the tall slice matrices
+  int64_t offset;  // element offset of H and D in the packed input/output
+};
+
+struct InstanceInfo {
+  double emin, emax, idem;
+  int32_t converged, pad;
+  unsigned long long bits[4];
+};
+
+struct Params {
+  const Instance* inst;   // [batch]
+  const int32_t* order;   // [batch] instance indices, largest first
+  int32_t* queue;         // work counter (zeroed before the launch)
+  int32_t batch;
+  int32_t rule;
+  int32_t maxiter;
+  int32_t pitch;          // P = max padded order (row pitch of the slice matrices)
+  int64_t total_rows;     // sum of padded orders
+  double tol;
+  const double* H;        // packed inputs
+  double* D;              // packed outputs
+  uint16_t* sl[2][2];     // [set][slice] tall FP16x2 slice matrices, total_rows x pitch
+  int32_t* iters;         // [batch] products per instance (may be null)
+  int32_t* status;        // [batch] progress_status_t per instance (may be null)
+  InstanceInfo* info;     // [batch] optional details
+};
+
+size_t smem_bytes();
+cudaError_t launch(const Params& prm, int grid, cudaStream_t s);
+
+}  // namespace batched
+}  // namespace sp2

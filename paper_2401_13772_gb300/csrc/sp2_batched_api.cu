@@ -1,0 +1,242 @@
+// C ABI of the batched solver: layout planning on the host (padded orders,
+// tall-matrix rows, largest-first order), a cached per-stream workspace and a
+// cached CUDA graph holding the queue reset and the one persistent launch.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <utility>
+#include <vector>
+
+#include "progress_sp2.h"
+#include "sp2_batched.h"
+#include "sp2_launch.h"
+
+namespace {
+
+using sp2::batched::Instance;
+using sp2::batched::InstanceInfo;
+using sp2::batched::Params;
+
+struct BatchWs {
+  cudaStream_t cap = nullptr;
+  // device buffers
+  uint16_t* sl[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  size_t slice_elems = 0;
+  Instance* inst = nullptr;
+  int32_t* order = nullptr;
+  int32_t* queue = nullptr;
+  InstanceInfo* info = nullptr;
+  int cap_batch = 0;
+  // cached graph of the last launch
+  cudaGraphExec_t exec = nullptr;
+  std::vector<Instance> last_inst;
+  Params last_prm{};
+  bool have_last = false;
+};
+
+std::mutex g_bmu;
+std::map<std::pair<int, cudaStream_t>, BatchWs*> g_bws;
+
+progress_status_t bfail(progress_status_t s, const char* what) {
+  sp2::set_last_error(what);
+  return s;
+}
+
+progress_status_t bcuda(cudaError_t e, const char* where) {
+  sp2::set_last_error(where);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? PROGRESS_ENOMEM : PROGRESS_ECUDA;
+}
+
+void free_bufs(BatchWs* w) {
+  for (int k = 0; k < 2; ++k)
+    for (int j = 0; j < 2; ++j) {
+      if (w->sl[k][j]) cudaFree(w->sl[k][j]);
+      w->sl[k][j] = nullptr;
+    }
+  w->slice_elems = 0;
+}
+
+void free_meta(BatchWs* w) {
+  if (w->inst) cudaFree(w->inst);
+  if (w->order) cudaFree(w->order);
+  if (w->queue) cudaFree(w->queue);
+  if (w->info) cudaFree(w->info);
+  w->inst = nullptr;
+  w->order = nullptr;
+  w->queue = nullptr;
+  w->info = nullptr;
+  w->cap_batch = 0;
+}
+
+void drop_graph(BatchWs* w) {
+  if (w->exec) cudaGraphExecDestroy(w->exec);
+  w->exec = nullptr;
+  w->have_last = false;
+}
+
+bool same_params(const Params& a, const Params& b) { return memcmp(&a, &b, sizeof a) == 0; }
+
+}  // namespace
+
+extern "C" progress_status_t progress_sp2_batched(int32_t batch, const int32_t* h_n,
+                                                  const int64_t* h_offset, const int32_t* h_nocc,
+                                                  const double* dH, double tol, double* dD,
+                                                  int32_t* d_iters, int32_t* d_status,
+                                                  const progress_opts_t* opts, void* stream) {
+  progress_opts_t o;
+  if (opts) {
+    o = *opts;
+  } else {
+    progress_opts_default(&o);
+    o.prec = PROGRESS_FP32_SPLIT;
+  }
+  if (batch < 0) return bfail(PROGRESS_EINVAL, "batch must be >= 0");
+  if (batch == 0) return PROGRESS_OK;
+  if (!h_n || !h_offset || !h_nocc || !dH || !dD)
+    return bfail(PROGRESS_EINVAL, "NULL pointer argument");
+  if (!(tol >= 0.0)) return bfail(PROGRESS_EINVAL, "tol must be >= 0");
+  if (o.prec != PROGRESS_FP32_SPLIT)
+    return bfail(PROGRESS_EUNSUPPORTED, "the batched solver runs PROGRESS_FP32_SPLIT only");
+  if (o.rule != PROGRESS_RULE_NEARER && o.rule != PROGRESS_RULE_PAPER)
+    return bfail(PROGRESS_EINVAL, "unknown branch rule");
+  if (o.maxiter < 0 || o.maxiter > 250) return bfail(PROGRESS_EINVAL, "maxiter must be in [0, 250]");
+  std::vector<Instance> inst(batch);
+  int pitch = 0;
+  int64_t rows = 0;
+  for (int i = 0; i < batch; ++i) {
+    const int n = h_n[i];
+    if (n < 1 || n > 4096) return bfail(PROGRESS_EINVAL, "every n_i must be in [1, 4096]");
+    if (h_nocc[i] < 0 || h_nocc[i] > n) return bfail(PROGRESS_EINVAL, "nocc_i must be in [0, n_i]");
+    if (h_offset[i] < 0) return bfail(PROGRESS_EINVAL, "offsets must be >= 0");
+    Instance& t = inst[i];
+    memset(&t, 0, sizeof t);
+    t.n = n;
+    t.m = (n + 127) / 128 * 128;
+    t.nocc = h_nocc[i];
+    t.row0 = rows;
+    t.offset = h_offset[i];
+    rows += t.m;
+    pitch = std::max(pitch, t.m);
+  }
+  int dev = 0, major = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return bcuda(e, "device query");
+  if (major != 10) return bfail(PROGRESS_EUNSUPPORTED, "the batched solver needs an sm_10x GPU");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  BatchWs* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto key = std::make_pair(dev, s);
+    auto it = g_bws.find(key);
+    if (it == g_bws.end()) {
+      w = new BatchWs();
+      if (cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        delete w;
+        return bcuda(cudaErrorUnknown, "capture stream");
+      }
+      g_bws[key] = w;
+    } else {
+      w = it->second;
+    }
+  }
+  // workspace
+  const size_t need = (size_t)rows * pitch;
+  if (need > w->slice_elems || batch > w->cap_batch) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bcuda(e, "cudaStreamSynchronize");
+    drop_graph(w);
+  }
+  if (need > w->slice_elems) {
+    free_bufs(w);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+        e = cudaMalloc(&w->sl[k][j], need * sizeof(uint16_t));
+    if (e != cudaSuccess) {
+      free_bufs(w);
+      return bcuda(e, "batched slice allocation");
+    }
+    w->slice_elems = need;
+  }
+  if (batch > w->cap_batch) {
+    free_meta(w);
+    e = cudaMalloc(&w->inst, batch * sizeof(Instance));
+    if (e == cudaSuccess) e = cudaMalloc(&w->order, batch * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&w->queue, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&w->info, batch * sizeof(InstanceInfo));
+    if (e != cudaSuccess) {
+      free_meta(w);
+      return bcuda(e, "batched metadata allocation");
+    }
+    w->cap_batch = batch;
+  }
+  // largest-first order (cost ~ m^3; ties keep the input order)
+  std::vector<int32_t> order(batch);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return inst[a].m > inst[b].m; });
+
+  Params prm;
+  memset(&prm, 0, sizeof prm);
+  prm.inst = w->inst;
+  prm.order = w->order;
+  prm.queue = w->queue;
+  prm.batch = batch;
+  prm.rule = o.rule;
+  prm.maxiter = o.maxiter;
+  prm.pitch = pitch;
+  prm.total_rows = rows;
+  prm.tol = tol;
+  prm.H = dH;
+  prm.D = dD;
+  for (int k = 0; k < 2; ++k)
+    for (int j = 0; j < 2; ++j) prm.sl[k][j] = w->sl[k][j];
+  prm.iters = d_iters;
+  prm.status = d_status;
+  prm.info = w->info;
+
+  const bool same_layout = w->have_last && w->last_inst.size() == inst.size() &&
+                           memcmp(w->last_inst.data(), inst.data(),
+                                  inst.size() * sizeof(Instance)) == 0;
+  if (!same_layout) {
+    // metadata upload (ordered on the stream before the launch)
+    e = cudaMemcpyAsync(w->inst, inst.data(), batch * sizeof(Instance), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(w->order, order.data(), batch * sizeof(int32_t), cudaMemcpyHostToDevice,
+                          s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors go out of scope
+    if (e != cudaSuccess) return bcuda(e, "batched metadata upload");
+  }
+  if (!(same_layout && w->exec && same_params(prm, w->last_prm))) {
+    drop_graph(w);
+    const int grid = std::min(batch, sms > 0 ? sms : 152);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(w->queue, 0, sizeof(int32_t), w->cap);
+      if (d_status) cudaMemsetAsync(d_status, 0xFF, batch * sizeof(int32_t), w->cap);
+      const cudaError_t le = sp2::batched::launch(prm, grid, w->cap);
+      e = cudaStreamEndCapture(w->cap, &g);
+      if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&w->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      drop_graph(w);
+      return bcuda(e, "batched graph capture");
+    }
+    w->last_inst = inst;
+    w->last_prm = prm;
+    w->have_last = true;
+  }
+  e = cudaGraphLaunch(w->exec, s);
+  if (e != cudaSuccess) return bcuda(e, "batched graph launch");
+  return PROGRESS_OK;
+}

@@ -1,0 +1,112 @@
+"""Batched split-precision SP2 (one persistent launch) against the CPU oracle.
+
+Each instance is compared element by element with the oracle's plain FP64 SP2
+(itself pinned to the spectral projector on the CPU). The batched solver runs
+split FP16 hi+lo products with FP32 accumulation and no FP64 refinement, so
+its accuracy is that of FP32 SP2: the gate below is the mixed-path gate
+scaled by the round-off of 22-bit operands over the small gaps these random
+parts have (max |D - D_ref| <= 1e-4), and the occupation must be exact to
+|Tr D - Nocc| <= 1e-3.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import batch_instance, cube_hamiltonian
+
+pytestmark = pytest.mark.gpu
+
+TOL_BATCH = 1e-4
+TOL_TRACE = 1e-3
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a CUDA device"
+    from paper_2401_13772_gb300.build import build
+    build()
+    import paper_2401_13772_gb300 as p
+    p.load()
+    return p
+
+
+def run_batch(pkg, mats, noccs, tol=1e-10):
+    import torch
+    packed, n, offsets = pkg.pack_batch(mats)
+    Hd = torch.from_numpy(packed).to("cuda:0")
+    D, iters, status = pkg.sp2_batched(Hd, n, offsets, noccs, tol)
+    torch.cuda.synchronize()
+    Dh = D.cpu().numpy()
+    outs = [Dh[o:o + k * k].reshape(k, k) for o, k in zip(offsets, n)]
+    return outs, iters.cpu().numpy(), status.cpu().numpy()
+
+
+def test_batched_matches_oracle_uneven_sizes(pkg):
+    rng = np.random.default_rng(7)
+    sites = list(rng.integers(16, 65, size=24)) + [192, 150, 100]
+    mats, noccs = [], []
+    for i, s in enumerate(sites):
+        H, nocc = batch_instance(i, int(s))
+        mats.append(H)
+        noccs.append(nocc)
+    outs, iters, status = run_batch(pkg, mats, noccs)
+    errs = []
+    for H, nocc, D, it, stt in zip(mats, noccs, outs, iters, status):
+        ref = oracle.sp2_plain(H, nocc, 1e-10)
+        assert stt == 0, stt
+        err = float(np.abs(D - ref["D"]).max())
+        errs.append(err)
+        assert abs(np.trace(D) - nocc) <= TOL_TRACE
+        assert abs(int(it) - ref["iters"]) <= 12
+    print("batched max errors:", sorted(errs)[-5:])
+    assert max(errs) <= TOL_BATCH
+
+
+def test_batched_equals_dense_split_in_distribution(pkg):
+    """Same arithmetic family as the dense FP32-split solve: errors of the same order."""
+    import torch
+    H, nocc = cube_hamiltonian(96, 31)  # n = 384
+    outs, iters, status = run_batch(pkg, [H, H], [nocc, nocc])
+    ref = oracle.sp2_plain(H, nocc, 1e-10)["D"]
+    Dd, info = pkg.sp2_dense_ex(torch.from_numpy(H).to("cuda:0"), nocc, 1e-10, prec="fp32_split")
+    e_dense = float(np.abs(Dd.cpu().numpy() - ref).max())
+    e_b = float(np.abs(outs[0] - ref).max())
+    assert np.array_equal(outs[0], outs[1])  # deterministic across CTAs
+    assert e_b <= max(10 * e_dense, 1e-6)
+
+
+def test_batched_degenerate_instances(pkg):
+    mats = [np.array([[0.3]]), np.array([[0.3]]), np.diag(np.linspace(-1, 1, 70)),
+            cube_hamiltonian(20, 3)[0], cube_hamiltonian(20, 3)[0]]
+    noccs = [0, 1, 31, 0, 80]
+    outs, iters, status = run_batch(pkg, mats, noccs)
+    assert list(status) == [0] * 5
+    assert abs(outs[0][0, 0]) <= 1e-6 and abs(outs[1][0, 0] - 1.0) <= 1e-6
+    expect = np.zeros(70)
+    expect[:31] = 1.0
+    assert np.abs(outs[2] - np.diag(expect)).max() <= 1e-5
+    assert np.abs(outs[3]).max() <= 1e-5
+    assert np.abs(outs[4] - np.eye(80)).max() <= 1e-5
+
+
+def test_batched_rejects_bad_arguments(pkg):
+    import ctypes
+    from paper_2401_13772_gb300 import _lib
+    lib = pkg.load()
+    n = np.array([4, 0], dtype=np.int32)
+    off = np.array([0, 16], dtype=np.int64)
+    no = np.array([2, 0], dtype=np.int32)
+    st = lib.progress_sp2_batched(2, ctypes.c_void_p(n.ctypes.data),
+                                  ctypes.c_void_p(off.ctypes.data),
+                                  ctypes.c_void_p(no.ctypes.data), ctypes.c_void_p(8), 1e-9,
+                                  ctypes.c_void_p(16), None, None, None, None)
+    assert st == _lib.EINVAL
+    o = pkg.make_opts(prec="fp64")
+    n[1] = 4
+    st = lib.progress_sp2_batched(2, ctypes.c_void_p(n.ctypes.data),
+                                  ctypes.c_void_p(off.ctypes.data),
+                                  ctypes.c_void_p(no.ctypes.data), ctypes.c_void_p(8), 1e-9,
+                                  ctypes.c_void_p(16), None, None, ctypes.byref(o), None)
+    assert st == _lib.EUNSUPPORTED
