@@ -37,6 +37,9 @@ METRIC = "SP2 solves/s & tensor TFLOP/s vs plain FP64 SP2, same GB300, at stated
 UNIT = "solves/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 NOMINAL_BF16_TFLOPS = 2250.0
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
+# stands, keyed by (kernel, n); see profiles/.
+NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200}
 NOMINAL_FP64_TFLOPS = 1.25
 
 
@@ -315,7 +318,8 @@ def main():
     def roof(kernel, ms, peak, note):
         ach = flops_alg / (ms * 1e-3) / 1e12
         return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "kernel": kernel, "peak_source": note,
+                "frac": ach / peak, "traffic": NCU_TRAFFIC.get((kernel, n)), "kernel": kernel,
+                "peak_source": note,
                 "flops_per_launch": flops_alg, "avg_launch_ms": ms}
 
     note64 = f"fp64: {peak_src} bf16 burst x nominal fp64/bf16 ratio (1.25/2250)"

@@ -130,6 +130,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int n = in.n, m = in.m, T = m / BM;
     const double* __restrict__ H = prm.H + in.offset;
     State& st = sh.st;
+    // A run with predicted bounds/bits that the judge rejects (or that
+    // diverges) is restarted once on the plain path.
+    bool predicted = prm.bounds_in != nullptr || prm.pred_bits != nullptr;
+    bool fell_back = false;
+  restart:
 
     // ---- set-up: state, Gershgorin bounds, X0 (all threads)
     {
@@ -171,6 +176,18 @@ __global__ void __launch_bounds__(THREADS, 1)
       st.tol = prm.tol;
       st.emin = lo;
       st.emax = hi;
+      if (predicted && prm.bounds_in) {
+        const double e0 = prm.bounds_in[2 * inst], e1 = prm.bounds_in[2 * inst + 1];
+        if (isfinite(e0) && isfinite(e1) && e1 > e0) {
+          st.emin = e0;
+          st.emax = e1;
+        }
+      }
+      if (predicted && prm.pred_bits && prm.pred_len) {
+        for (int b = 0; b < 4; ++b) st.pred_bits[b] = prm.pred_bits[4 * inst + b];
+        st.pred_len = min(prm.pred_len[inst], kMaxHist);
+        st.judge_delta = prm.judge_delta;
+      }
       st.best_split_idem = INFINITY;
       st.phase = kPhaseSplit;
     }
@@ -346,6 +363,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       __syncthreads();
     }
 
+    if (predicted && !*err && (st.judge_fail || st.status == PROGRESS_EBOUNDS ||
+                               st.status == PROGRESS_ENOCONV)) {
+      predicted = false;
+      fell_back = true;
+      __syncthreads();
+      goto restart;
+    }
+
     // ---- D (FP64, n x n at the instance's offset) from the final slices
     {
       const int fin = st.iter & 1;
@@ -359,6 +384,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (threadIdx.x == 0) {
         if (prm.iters) prm.iters[inst] = st.iter;
+        if (prm.fallback) prm.fallback[inst] = fell_back ? 1 : 0;
+        if (prm.bits_out)
+          for (int b = 0; b < 4; ++b) prm.bits_out[4 * inst + b] = st.bits[b];
+        if (prm.bounds_out) {
+          prm.bounds_out[2 * inst] = st.emin;
+          prm.bounds_out[2 * inst + 1] = st.emax;
+        }
         if (prm.status) prm.status[inst] = st.status;
         if (prm.info) {
           InstanceInfo& o = prm.info[inst];

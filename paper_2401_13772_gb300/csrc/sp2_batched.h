@@ -35,6 +35,14 @@ struct Params {
   const double* H;        // packed inputs
   double* D;              // packed outputs
   uint16_t* sl[2][2];     // [set][slice] tall FP16x2 slice matrices, total_rows x pitch
+  // learned-sequence inputs/outputs (all optional)
+  const double* bounds_in;               // [batch][2] emin, emax (NaN = Gershgorin)
+  const unsigned long long* pred_bits;   // [batch][4]
+  const int32_t* pred_len;               // [batch]
+  double judge_delta;
+  unsigned long long* bits_out;          // [batch][4]
+  double* bounds_out;                    // [batch][2]
+  int32_t* fallback;                     // [batch]
   int32_t* iters;         // [batch] products per instance (may be null)
   int32_t* status;        // [batch] progress_status_t per instance (may be null)
   InstanceInfo* info;     // [batch] optional details

@@ -48,6 +48,12 @@ struct State {
   int x_slices_valid; // the current iterate X_k is stored as slices (set k % 2)
   unsigned int ticket;  // CTA arrival counter of the running launch
   double best_split_idem;
+  // learned-sequence judge: predicted branch bits and the margin beyond which
+  // a disagreement with the trace rule aborts the predicted run
+  unsigned long long pred_bits[4];
+  int pred_len;
+  int judge_fail;
+  double judge_delta;
   unsigned long long bits[4];
   double idem_hist[kMaxHist];
   double margin_hist[kMaxHist];
@@ -135,14 +141,15 @@ __device__ inline void decide(State* st) {
       // round-off floor. Plateaus of the error above 0.01 are not that floor:
       // each eigenvalue still between 0.01 and 0.99 adds at least 0.0099, and
       // SP2 holds the last few pairs around the gap near 0.5 for many steps
-      // while it separates them (and the first steps oscillate far above 1).
-      // So: two steps without a 0.1 % improvement below 0.01, or eight below 1.
+      // while it separates them (one pair at 0.5 alone contributes 0.5, and
+      // the first steps oscillate far above 1). So: two steps without a 0.1 %
+      // improvement below 0.01, or eight below 0.1.
       if (idem < st->best_split_idem * 0.999) {
         st->best_split_idem = idem;
         st->split_stall = 0;
       } else {
         ++st->split_stall;
-        if ((st->split_stall >= 2 && idem < 0.01) || (st->split_stall >= 8 && idem < 1.0))
+        if ((st->split_stall >= 2 && idem < 0.01) || (st->split_stall >= 8 && idem < 0.1))
           stalled = true;
       }
     }
@@ -177,6 +184,21 @@ __device__ inline void decide(State* st) {
     const double d_expand = fabs(2.0 * t1 - t2 - nocc);
     margin = d_square - d_expand;
     b = margin > 1e-12 * fmax(n, 1.0) ? 1 : 0;
+  }
+  if (k < st->pred_len) {
+    // Judge of a predicted branch sequence: the trace rule still runs; a
+    // disagreement beyond the margin stops this run (the caller restarts the
+    // instance on the plain path), a near-tie follows the prediction.
+    const int pb = (int)((st->pred_bits[k >> 6] >> (k & 63)) & 1ull);
+    if (pb != b) {
+      if (fabs(margin) > st->judge_delta) {
+        st->judge_fail = 1;
+        st->done = 1;
+        if (k < kMaxHist) st->margin_hist[k] = margin;
+        return;
+      }
+      b = pb;
+    }
   }
   st->bit = b;
   if (k < kMaxHist) {
