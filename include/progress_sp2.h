@@ -181,6 +181,83 @@ progress_status_t progress_sp2_batched(int32_t batch, const int32_t* h_n, const 
                                        double* dD, int32_t* d_iters, int32_t* d_status,
                                        const progress_opts_t* opts, void* stream);
 
+/* Learned-sequence inputs and outputs of a batched solve (all optional). */
+typedef struct {
+  const double* d_bounds;      /* device [batch][2]: emin, emax to use for X0 (NaN = Gershgorin) */
+  const uint64_t* d_pred_bits; /* device [batch][4]: predicted branch of product k = bit k */
+  const int32_t* d_pred_len;   /* device [batch]: number of predicted branches */
+  double judge_delta;          /* a predicted branch that disagrees with the trace rule by a
+                                  margin > judge_delta (trace units) rejects the prediction */
+  uint64_t* d_bits_out;        /* device [batch][4]: branches taken, or NULL */
+  double* d_bounds_out;        /* device [batch][2]: bounds used, or NULL */
+  int32_t* d_fallback;         /* device [batch]: 1 if the instance reverted to the plain
+                                  path (Gershgorin bounds, trace rule), or NULL */
+  int32_t reserved[8];         /* must be zero */
+} progress_batch_ex_t;
+
+/*
+ * progress_sp2_batched with learned inputs. An instance given predicted
+ * bounds and/or branch bits runs SP2 with them; the trace rule is still
+ * evaluated at every product and judges each predicted branch. On a
+ * disagreement beyond judge_delta, or if the run leaves [0, 1] or does not
+ * converge, that instance alone restarts from X0 with Gershgorin bounds and
+ * the plain trace-driven rule (d_fallback = 1).
+ */
+progress_status_t progress_sp2_batched_ex(int32_t batch, const int32_t* h_n,
+                                          const int64_t* h_offset, const int32_t* h_nocc,
+                                          const double* dH, double tol, double* dD,
+                                          int32_t* d_iters, int32_t* d_status,
+                                          const progress_opts_t* opts,
+                                          const progress_batch_ex_t* ex, void* stream);
+
+/*
+ * Features of the learned predictor, 37 floats per instance (device output
+ * [batch][37]): Gershgorin emin/w, emax/w (w = emax - emin, §VIII.A),
+ * Tr H/(n w), ||H||_F/(sqrt(n) w), a 32-bin histogram of diag(H) over
+ * [emin, emax] divided by n, and n/2048. d_n, d_offset are DEVICE arrays,
+ * H packed as for progress_sp2_batched.
+ */
+progress_status_t progress_features(int32_t batch, const int32_t* d_n, const int64_t* d_offset,
+                                    const double* dH, float* d_feat, void* stream);
+
+/* d_out[i] = Tr(H_i D_i) for packed symmetric H and D (device arrays). With D
+ * the projector onto the lowest state (nocc = 1) this is that state's energy. */
+progress_status_t progress_trace_hd(int32_t batch, const int32_t* d_n, const int64_t* d_offset,
+                                    const double* dH, const double* dD, double* d_out,
+                                    void* stream);
+
+/*
+ * The predictor: a perceptron in -> hidden (ReLU) -> hidden (ReLU) -> out.
+ * Parameters are one flat FP32 vector: W1 [hidden][in], b1, W2 [hidden][hidden],
+ * b2, W3 [out][hidden], b3. Outputs 0 and 1 are the bound fractions
+ * u_min = (eps_1 - emin)/w and u_max = (emax - eps_N)/w; outputs 2.. are the
+ * logits of the branch bits. The loss (mean over the batch) is
+ *   sum_{j<2} c (y_j - t_j)^2, c = 10 if y_j > t_j else 1   (over-shooting a
+ *   bound would cut the spectrum)
+ * + sum_{j>=2} mask_j BCE_with_logits(y_j, t_j) / max(1, sum_j mask_j).
+ */
+int32_t progress_mlp_param_count(int32_t in, int32_t hidden, int32_t out);
+/* Floats of device scratch that progress_mlp_train_step / _forward need. */
+int64_t progress_mlp_scratch_floats(int32_t in, int32_t hidden, int32_t out, int32_t batch);
+/* FP16 copy of the parameters (the inference weights). */
+progress_status_t progress_mlp_to_fp16(const float* d_params, int32_t count,
+                                       uint16_t* d_params_fp16, void* stream);
+/* y = mlp(x) with FP16 weights, FP32 arithmetic; x [batch][in], y [batch][out]. */
+progress_status_t progress_mlp_forward(int32_t in, int32_t hidden, int32_t out,
+                                       const uint16_t* d_params_fp16, int32_t batch,
+                                       const float* d_x, float* d_y, float* d_scratch,
+                                       void* stream);
+/* One training step: forward, loss (d_loss, 1 float, may be NULL), gradient
+ * into d_grad, then Adam (beta 0.9/0.999, eps 1e-8, bias-corrected with
+ * `step` >= 1) on d_params with moments d_m, d_v. lr = 0 computes the
+ * gradient only. All arrays are device FP32. */
+progress_status_t progress_mlp_train_step(int32_t in, int32_t hidden, int32_t out,
+                                          float* d_params, float* d_grad, float* d_m,
+                                          float* d_v, int32_t step, float lr, int32_t batch,
+                                          const float* d_x, const float* d_target,
+                                          const float* d_mask, float* d_scratch, float* d_loss,
+                                          void* stream);
+
 /* Synchronize `stream` and report the last solve queued on it. */
 progress_status_t progress_sp2_query(void* stream, progress_info_t* info);
 

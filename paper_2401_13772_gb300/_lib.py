@@ -45,6 +45,13 @@ class Info(ctypes.Structure):
                 "idempotency": self.idempotency, "bits": bits}
 
 
+class BatchEx(ctypes.Structure):
+    _fields_ = [("d_bounds", ctypes.c_void_p), ("d_pred_bits", ctypes.c_void_p),
+                ("d_pred_len", ctypes.c_void_p), ("judge_delta", ctypes.c_double),
+                ("d_bits_out", ctypes.c_void_p), ("d_bounds_out", ctypes.c_void_p),
+                ("d_fallback", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 8)]
+
+
 # symbol -> (restype, argtypes); every function declared in include/progress_sp2.h
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -58,6 +65,20 @@ SIGNATURES = {
     "progress_sp2_dense_noalloc": (ctypes.c_int, [_P, _I64, _I64, _D, _P, _P]),
     "progress_sp2_batched": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _D, _P, _P, _P,
                                             ctypes.POINTER(Opts), _P]),
+    "progress_sp2_batched_ex": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _D, _P, _P, _P,
+                                               ctypes.POINTER(Opts), ctypes.POINTER(BatchEx), _P]),
+    "progress_features": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P]),
+    "progress_trace_hd": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
+    "progress_mlp_param_count": (ctypes.c_int32, [ctypes.c_int32] * 3),
+    "progress_mlp_scratch_floats": (ctypes.c_int64, [ctypes.c_int32] * 4),
+    "progress_mlp_to_fp16": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "progress_mlp_forward": (ctypes.c_int, [ctypes.c_int32] * 3 + [_P, ctypes.c_int32, _P, _P,
+                                                                   _P, _P]),
+    "progress_mlp_train_step": (ctypes.c_int, [ctypes.c_int32] * 3 + [_P, _P, _P, _P,
+                                                                      ctypes.c_int32,
+                                                                      ctypes.c_float,
+                                                                      ctypes.c_int32, _P, _P, _P,
+                                                                      _P, _P, _P]),
     "progress_sp2_query": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "progress_sp2_history": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
     "progress_release": (ctypes.c_int, [_P]),

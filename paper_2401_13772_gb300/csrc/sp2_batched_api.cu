@@ -81,6 +81,11 @@ void drop_graph(BatchWs* w) {
 
 bool same_params(const Params& a, const Params& b) { return memcmp(&a, &b, sizeof a) == 0; }
 
+progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t* h_offset,
+                               const int32_t* h_nocc, const double* dH, double tol, double* dD,
+                               int32_t* d_iters, int32_t* d_status, const progress_opts_t* opts,
+                               const progress_batch_ex_t* ex, void* stream);
+
 }  // namespace
 
 extern "C" progress_status_t progress_sp2_batched(int32_t batch, const int32_t* h_n,
@@ -88,6 +93,27 @@ extern "C" progress_status_t progress_sp2_batched(int32_t batch, const int32_t* 
                                                   const double* dH, double tol, double* dD,
                                                   int32_t* d_iters, int32_t* d_status,
                                                   const progress_opts_t* opts, void* stream) {
+  return batched_impl(batch, h_n, h_offset, h_nocc, dH, tol, dD, d_iters, d_status, opts, nullptr,
+                      stream);
+}
+
+extern "C" progress_status_t progress_sp2_batched_ex(int32_t batch, const int32_t* h_n,
+                                                     const int64_t* h_offset,
+                                                     const int32_t* h_nocc, const double* dH,
+                                                     double tol, double* dD, int32_t* d_iters,
+                                                     int32_t* d_status,
+                                                     const progress_opts_t* opts,
+                                                     const progress_batch_ex_t* ex, void* stream) {
+  return batched_impl(batch, h_n, h_offset, h_nocc, dH, tol, dD, d_iters, d_status, opts, ex,
+                      stream);
+}
+
+namespace {
+
+progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t* h_offset,
+                               const int32_t* h_nocc, const double* dH, double tol, double* dD,
+                               int32_t* d_iters, int32_t* d_status, const progress_opts_t* opts,
+                               const progress_batch_ex_t* ex, void* stream) {
   progress_opts_t o;
   if (opts) {
     o = *opts;
@@ -201,6 +227,15 @@ extern "C" progress_status_t progress_sp2_batched(int32_t batch, const int32_t* 
   prm.iters = d_iters;
   prm.status = d_status;
   prm.info = w->info;
+  if (ex) {
+    prm.bounds_in = ex->d_bounds;
+    prm.pred_bits = reinterpret_cast<const unsigned long long*>(ex->d_pred_bits);
+    prm.pred_len = ex->d_pred_len;
+    prm.judge_delta = ex->judge_delta;
+    prm.bits_out = reinterpret_cast<unsigned long long*>(ex->d_bits_out);
+    prm.bounds_out = ex->d_bounds_out;
+    prm.fallback = ex->d_fallback;
+  }
 
   const bool same_layout = w->have_last && w->last_inst.size() == inst.size() &&
                            memcmp(w->last_inst.data(), inst.data(),
@@ -240,3 +275,5 @@ extern "C" progress_status_t progress_sp2_batched(int32_t batch, const int32_t* 
   if (e != cudaSuccess) return bcuda(e, "batched graph launch");
   return PROGRESS_OK;
 }
+
+}  // namespace

@@ -1,0 +1,150 @@
+"""Learned-sequence part on the GPU: features, perceptron gradients and Adam
+against the CPU oracle, the judge/fallback of predicted branches, and the
+gain of a trained predictor over the plain method."""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from workloads import batch_instance, cube_hamiltonian
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a CUDA device"
+    from paper_2401_13772_gb300.build import build
+    build()
+    import paper_2401_13772_gb300 as p
+    p.load()
+    from paper_2401_13772_gb300 import learned
+    return learned
+
+
+def test_features_match_oracle(L):
+    mats = [cube_hamiltonian(s, 40 + s)[0] for s in (16, 33, 70)] + [np.diag([0.5, -1.0, 2.0])]
+    b = L.to_device_batch(mats)
+    f = L.features(b).cpu().numpy()
+    for H, row in zip(mats, f):
+        ref = omlp.features(H)
+        assert np.abs(row[:4] - ref[:4]).max() <= 1e-5 * max(1.0, np.abs(ref[:4]).max())
+        assert np.array_equal(row[4:36], ref[4:36].astype(np.float32))
+        assert abs(row[36] - ref[36]) <= 1e-7
+
+
+def test_trace_hd_and_extremal_eigenvalues(L):
+    import torch
+    mats = [cube_hamiltonian(s, 7 + s)[0] for s in (20, 48, 96)]
+    b = L.to_device_batch(mats)
+    D = torch.from_numpy(np.concatenate([np.eye(m.shape[0]).ravel() for m in mats])).cuda()
+    t = L.trace_hd(b, D).cpu().numpy()
+    assert np.allclose(t, [np.trace(m) for m in mats], atol=1e-4)
+    e1, eN, lo, hi = L.extremal_eigenvalues(b)
+    for H, a, z, g0, g1 in zip(mats, e1.cpu().numpy(), eN.cpu().numpy(), lo.cpu().numpy(),
+                               hi.cpu().numpy()):
+        w = np.linalg.eigvalsh(H)
+        emin, emax = oracle.gershgorin_bounds(H)
+        assert abs(g0 - emin) < 1e-9 and abs(g1 - emax) < 1e-9
+        # within the edge degeneracy: between the two lowest (highest) eigenvalues
+        assert w[0] - 1e-3 <= a <= w[1] + 1e-3
+        assert w[-2] - 1e-3 <= z <= w[-1] + 1e-3
+
+
+def _rand_problem(seed, B=40, kmax=12, hidden=32):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((B, omlp.N_FEAT)).astype(np.float32)
+    T = np.concatenate([rng.uniform(0, 0.3, (B, 2)), rng.uniform(size=(B, kmax)) > 0.5], 1)
+    M = np.concatenate([np.ones((B, 2)), rng.uniform(size=(B, kmax)) > 0.2], 1)
+    return X, T.astype(np.float32), M.astype(np.float32), hidden, kmax
+
+
+def test_gradient_and_adam_match_oracle(L):
+    import torch
+    X, T, M, hid, kmax = _rand_problem(1)
+    P = L.Predictor(hidden=hid, kmax=kmax, seed=3)
+    p0 = P.params.cpu().numpy().astype(np.float64)
+    Xd, Td, Md = (torch.from_numpy(a).cuda() for a in (X, T, M))
+    g, loss = P.gradient(Xd, Td, Md)
+    lref, gref = omlp.loss_and_grad(p0, X.astype(np.float64), T.astype(np.float64),
+                                    M.astype(np.float64), omlp.N_FEAT, hid, 2 + kmax)
+    g = g.cpu().numpy()
+    assert abs(float(loss) - lref) <= 1e-5 * max(1.0, lref)
+    assert np.abs(g - gref).max() <= 1e-4 * max(1.0, np.abs(gref).max())
+    # one Adam step (step 1) against the oracle's update
+    P.train_step(Xd, Td, Md, 1e-2)
+    p1, _, _ = omlp.adam_step(p0, gref, np.zeros_like(p0), np.zeros_like(p0), 1, 1e-2)
+    assert np.abs(P.params.cpu().numpy() - p1).max() <= 1e-5
+
+
+def test_forward_fp16_matches_oracle_with_rounded_weights(L):
+    import torch
+    X, T, M, hid, kmax = _rand_problem(2)
+    P = L.Predictor(hidden=hid, kmax=kmax, seed=4)
+    Y = P.predict(torch.from_numpy(X).cuda()).cpu().numpy()
+    ph = P.params.cpu().numpy().astype(np.float16).astype(np.float64)
+    Yref, _ = omlp.mlp_forward(ph, X.astype(np.float64), omlp.N_FEAT, hid, 2 + kmax)
+    assert np.abs(Y - Yref).max() <= 1e-4 * max(1.0, np.abs(Yref).max())
+
+
+def test_judge_rejects_wrong_predictions_and_keeps_d(L):
+    import torch
+    mats = [batch_instance(i, 40)[0] for i in range(4)]
+    nocc = [m.shape[0] // 2 for m in mats]
+    b = L.to_device_batch(mats)
+    plain = L.batched_solve(b, nocc)
+    B = len(mats)
+    # predicted bits = complement of the real sequence: rejected at the first
+    # product with a clear margin
+    wrong = (~plain["bits"]).contiguous()
+    plen = torch.full((B,), 60, dtype=torch.int32, device="cuda:0")
+    r = L.batched_solve(b, nocc, pred_bits=wrong, pred_len=plen, judge_delta=1e-3)
+    assert r["fallback"].cpu().numpy().tolist() == [1] * B
+    assert torch.equal(r["iters"], plain["iters"])
+    assert (r["D"] - plain["D"]).abs().max().item() <= 1e-6
+    # bounds that cut the spectrum: the run leaves [0, 1] and falls back
+    lo, hi = plain["bounds"][:, 0], plain["bounds"][:, 1]
+    bad = torch.stack([lo + 0.6 * (hi - lo), hi], 1).contiguous()
+    r = L.batched_solve(b, nocc, bounds=bad)
+    assert r["fallback"].cpu().numpy().tolist() == [1] * B
+    assert (r["D"] - plain["D"]).abs().max().item() <= 1e-6
+    # the real sequence and exact-ish bounds are accepted
+    e1, eN, g0, g1 = L.extremal_eigenvalues(b)
+    w = g1 - g0
+    good = torch.stack([e1 - 0.02 * w, eN + 0.02 * w], 1).contiguous()
+    r = L.batched_solve(b, nocc, bounds=good)
+    assert r["fallback"].sum().item() == 0
+    assert (r["iters"] <= plain["iters"]).all()
+
+
+def test_trained_predictor_saves_iterations(L):
+    """Train on SP2-labelled cube instances, evaluate on fresh ones: fewer
+    products than the plain method, D still within the batched gate."""
+    import torch
+    rng = np.random.default_rng(11)
+    train_sites = rng.integers(32, 129, size=160)
+    eval_sites = rng.integers(64, 129, size=40)
+    margin, kmax = 0.01, 80
+    tr = L.to_device_batch([cube_hamiltonian(int(s), 10000 + i)[0]
+                            for i, s in enumerate(train_sites)])
+    lab = L.label_batch(tr, [int(2 * s) for s in train_sites], margin, kmax)
+    P = L.Predictor(hidden=128, kmax=kmax, seed=0)
+    losses = P.fit(lab["X"], lab["T"], lab["M"], epochs=150, batch=64, lr=2e-3)
+    assert losses[-1] < losses[0]
+    mats = [cube_hamiltonian(int(s), 50000 + i)[0] for i, s in enumerate(eval_sites)]
+    ev = L.to_device_batch(mats)
+    nocc = [m.shape[0] // 2 for m in mats]
+    plain = L.batched_solve(ev, nocc)
+    lr = L.solve_learned(P, ev, nocc, plain["bounds"][:, 0], plain["bounds"][:, 1], margin,
+                         judge_delta=0.05)
+    it_plain = plain["iters"].double().mean().item()
+    it_learn = lr["iters"].double().mean().item()
+    fb = lr["fallback"].double().mean().item()
+    print(f"iterations plain {it_plain:.2f} learned {it_learn:.2f} fallback rate {fb:.2f}")
+    assert it_learn < it_plain
+    Dl = lr["D"].cpu().numpy()
+    for H, no, o, k in zip(mats[:6], nocc, ev["offsets"], ev["n"]):
+        ref = oracle.sp2_plain(H, no, 1e-10)["D"]
+        assert np.abs(Dl[o:o + k * k].reshape(k, k) - ref).max() <= 1e-4
