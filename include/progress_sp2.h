@@ -57,7 +57,11 @@ typedef enum {
                                cores with FP32 accumulation (~FP32 accuracy) */
   PROGRESS_MIXED_FP16 = 2,  /* fp64_prefix FP64 products, then fp16 hi+lo split products, then
                                FP64 refinement products until idempotent in FP64 */
-  PROGRESS_MIXED_BF16 = 3   /* as MIXED_FP16 with bf16 hi+mid+lo (3-way) splits */
+  PROGRESS_MIXED_BF16 = 3,  /* as MIXED_FP16 with bf16 hi+mid+lo (3-way) splits */
+  PROGRESS_FP32_SPLIT_BF16 = 4 /* as FP32_SPLIT with bf16 hi+mid+lo splits: six products
+                               instead of three, but FP32's exponent range (fp16 slices
+                               flush entries below ~6e-8, which runs with nocc << n reach
+                               by repeated squaring) */
 } progress_prec_t;
 
 typedef enum {
@@ -171,8 +175,9 @@ progress_status_t progress_sp2_dense_noalloc(const double* dH, int64_t n, int64_
  *   dD  device, packed outputs with the same layout; written
  *   d_iters, d_status  device int32 [batch] or NULL: products performed and
  *       progress_status_t per instance (-1 if the instance was not reached)
- *   opts  NULL or prec = PROGRESS_FP32_SPLIT (the only batched precision),
- *         rule, maxiter; other fields ignored
+ *   opts  NULL or prec = PROGRESS_FP32_SPLIT (fp16 hi+lo) or
+ *         PROGRESS_FP32_SPLIT_BF16 (bf16 hi+mid+lo), rule, maxiter; other fields
+ *         ignored
  * Asynchronous on `stream`. Errors: EINVAL (bad sizes), EUNSUPPORTED (other
  * precisions or a GPU without tcgen05), ENOMEM, ECUDA.
  */

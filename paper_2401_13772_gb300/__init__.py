@@ -18,7 +18,7 @@ import math
 
 from . import _lib
 from ._lib import (  # noqa: F401
-    FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16, RULE_NEARER, RULE_PAPER,
+    FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16, FP32_SPLIT_BF16, RULE_NEARER, RULE_PAPER,
     Info, Opts, ProgressError, load, check,
 )
 
@@ -27,7 +27,7 @@ __all__ = ["gershgorin_bounds", "sp2_dense", "sp2_dense_ex", "release", "load",
            "PREC_NAMES", "ProgressError"]
 
 PREC_NAMES = {"fp64": FP64, "fp32_split": FP32_SPLIT, "mixed_fp16": MIXED_FP16,
-              "mixed_bf16": MIXED_BF16}
+              "mixed_bf16": MIXED_BF16, "fp32_split_bf16": FP32_SPLIT_BF16}
 RULE_NAMES = {"nearer": RULE_NEARER, "paper": RULE_PAPER}
 
 
@@ -135,7 +135,7 @@ def pack_batch(mats):
 
 
 def sp2_batched(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", maxiter=100,
-                stream=None):
+                stream=None, prec="fp32_split"):
     """Batched split-precision SP2 over packed device inputs.
 
     H_packed: 1-D float64 CUDA tensor; n, offsets, nocc: host int sequences.
@@ -154,7 +154,7 @@ def sp2_batched(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", m
         D_packed = torch.empty_like(H_packed)
     iters = torch.zeros(b, dtype=torch.int32, device=H_packed.device)
     status = torch.zeros(b, dtype=torch.int32, device=H_packed.device)
-    o = make_opts(prec="fp32_split", rule=rule, maxiter=maxiter)
+    o = make_opts(prec=prec, rule=rule, maxiter=maxiter)
     with torch.cuda.device(H_packed.device):
         check(load().progress_sp2_batched(
             b, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(offsets.ctypes.data),

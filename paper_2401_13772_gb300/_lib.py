@@ -17,7 +17,7 @@ STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOCONV: "ENOCONV", EBOUNDS: "EBOUND
                 ECUDA: "ECUDA", ENOMEM: "ENOMEM", ETIMEOUT: "ETIMEOUT",
                 EUNSUPPORTED: "EUNSUPPORTED"}
 
-FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16 = range(4)
+FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16, FP32_SPLIT_BF16 = range(5)
 RULE_NEARER, RULE_PAPER = 0, 1
 
 

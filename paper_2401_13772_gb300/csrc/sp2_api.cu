@@ -306,8 +306,11 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   if (n < 0 || n > (1 << 16)) return fail(PROGRESS_EINVAL, "n must be in [0, 65536]");
   if (nocc < 0 || nocc > n) return fail(PROGRESS_EINVAL, "nocc must be in [0, n]");
   if (!(tol >= 0.0)) return fail(PROGRESS_EINVAL, "tol must be >= 0");
-  if (o.prec < PROGRESS_FP64 || o.prec > PROGRESS_MIXED_BF16)
+  if (o.prec < PROGRESS_FP64 || o.prec > PROGRESS_FP32_SPLIT_BF16)
     return fail(PROGRESS_EINVAL, "unknown precision mode");
+  // the all-split bf16 mode is the all-split mode with bf16 slices
+  const bool split_bf16 = o.prec == PROGRESS_FP32_SPLIT_BF16;
+  if (split_bf16) o.prec = PROGRESS_FP32_SPLIT;
   if (o.rule != PROGRESS_RULE_NEARER && o.rule != PROGRESS_RULE_PAPER)
     return fail(PROGRESS_EINVAL, "unknown branch rule");
   if (o.maxiter < 0 || o.maxiter > sp2::kMaxHist - 6)
@@ -338,7 +341,8 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   if (st != PROGRESS_OK) return st;
   const int ld = round_up(n, 128);
   const bool need_x64 = o.prec != PROGRESS_FP32_SPLIT;
-  const int fmt = slice_fmt_of(o.prec, o.slice_fixed);
+  int fmt = slice_fmt_of(o.prec, o.slice_fixed);
+  if (split_bf16) fmt = o.slice_fixed ? sp2::kBF16x3F : sp2::kBF16x3;
   const int nslices = o.prec == PROGRESS_FP64 ? 0 : sp2::fmt_slices(fmt);
   st = ensure_buffers(w, ld, need_x64, nslices);
   if (st != PROGRESS_OK) return st;

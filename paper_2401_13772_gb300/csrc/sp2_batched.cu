@@ -47,23 +47,30 @@ namespace {
 constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int TILE_BYTES = BM * BK * 2;  // one 128 x 64 slice box
-constexpr int NS = 2;                    // FP16x2
-constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
-constexpr int STAGES = 3;
 constexpr int THREADS = 256;
 constexpr int EPI_WARP0 = 4;             // warps 4..7 own tensor-memory lanes 0..127
-constexpr int TMEM_COLS = 512;           // 2 buffers x (acc0 | acc1)
-constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+constexpr int TMEM_COLS = 512;           // 2 buffers x 256 columns
+
+// FP16x2: acc0 (hi*hi) and acc1 (hi*lo + lo*hi, weight 2^-11) per buffer.
+// BF16x3: the slices carry their own magnitudes, so all six products go to
+// one accumulator per buffer.
+template <int F>
+struct BCfg {
+  static constexpr int NS = fmt_slices(F);
+  static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
+  static constexpr int STAGES = fmt_bf16(F) ? 2 : 3;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+};
 
 struct Maps {
-  CUtensorMap m[2][2];  // [set][slice]
+  CUtensorMap m[2][3];  // [set][slice]
 };
 
 struct Shared {
   State st;             // control state of the instance in flight
   double red[2 * THREADS / 32];
   double lo[THREADS / 32], hi[THREADS / 32];
-  uint64_t bars[2 * STAGES + 5];
+  uint64_t bars[2 * 3 + 5];
   int kb_consumed;
   uint32_t tmem;
   int err;
@@ -78,8 +85,12 @@ __device__ __forceinline__ void fence_async_global() {
   asm volatile("fence.proxy.async.global;\n" ::: "memory");
 }
 
+template <int F>
 __global__ void __launch_bounds__(THREADS, 1)
     batched_kernel(const __grid_constant__ Maps maps, Params prm) {
+  constexpr int NS = BCfg<F>::NS;
+  constexpr int STAGES = BCfg<F>::STAGES;
+  constexpr int STAGE_BYTES = BCfg<F>::STAGE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ Shared sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -113,7 +124,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
   volatile int* err = &sh.err;
-  constexpr uint32_t idesc = idesc_f16(0, BM, BM);
+  constexpr uint32_t idesc = idesc_f16(fmt_bf16(F) ? 1 : 0, BM, BM);
 
   // ring / buffer counters, each kept by the thread that uses it
   uint32_t kb_prod = 0, kb_mma = 0, tile_mma = 0, tile_epi = 0;
@@ -198,6 +209,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const float emax_f = (float)st.emax, inv_f = (float)(1.0 / (st.emax - st.emin));
       uint16_t* s0 = prm.sl[0][0];
       uint16_t* s1 = prm.sl[0][1];
+      uint16_t* s2 = prm.sl[0][2];
       double tr = 0.0, fr = 0.0;
       for (int r = warp; r < m; r += THREADS / 32) {
         float trf = 0.0f, frf = 0.0f;
@@ -211,9 +223,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             frf += x * x;
           }
           uint16_t a, b, c2;
-          split_value_f<kFP16x2>(x, a, b, c2);
+          split_value_f<F>(x, a, b, c2);
           s0[g0 + c] = a;
           s1[g0 + c] = b;
+          if (NS == 3) s2[g0 + c] = c2;
         }
         tr += (double)trf;
         fr += (double)frf;
@@ -270,16 +283,29 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (!mbar_wait(full_bar(s), ph, err)) break;
               tc_fence_after();
               const uint32_t sa = base + s * STAGE_BYTES;
-              const uint64_t a0 = smem_desc_sw128(sa), a1 = smem_desc_sw128(sa + TILE_BYTES);
-              const uint64_t b0 = smem_desc_sw128(sa + 2 * TILE_BYTES);
-              const uint64_t b1 = smem_desc_sw128(sa + 3 * TILE_BYTES);
+              uint64_t a[NS], b[NS];
+#pragma unroll
+              for (int j = 0; j < NS; ++j) {
+                a[j] = smem_desc_sw128(sa + j * TILE_BYTES);
+                b[j] = smem_desc_sw128(sa + (NS + j) * TILE_BYTES);
+              }
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint64_t adv = (uint64_t)(kk * 32) >> 4;
                 const uint32_t acc = (kb == 0 && kk == 0) ? 0u : 1u;
-                mma_f16(acc0, a0 + adv, b0 + adv, idesc, acc);
-                mma_f16(acc1, a0 + adv, b1 + adv, idesc, acc);
-                mma_f16(acc1, a1 + adv, b0 + adv, idesc, 1u);
+                if (NS == 2) {
+                  mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, acc);
+                  mma_f16(acc1, a[0] + adv, b[1] + adv, idesc, acc);
+                  mma_f16(acc1, a[1] + adv, b[0] + adv, idesc, 1u);
+                } else {
+                  // small terms first, the leading product last
+                  mma_f16(acc0, a[0] + adv, b[2 % NS] + adv, idesc, acc);
+                  mma_f16(acc0, a[2 % NS] + adv, b[0] + adv, idesc, 1u);
+                  mma_f16(acc0, a[1] + adv, b[1] + adv, idesc, 1u);
+                  mma_f16(acc0, a[0] + adv, b[1] + adv, idesc, 1u);
+                  mma_f16(acc0, a[1] + adv, b[0] + adv, idesc, 1u);
+                  mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, 1u);
+                }
               }
               mma_commit(empty_bar(s));
             }
@@ -293,8 +319,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const uint16_t* xs0 = prm.sl[src][0];
         const uint16_t* xs1 = prm.sl[src][1];
+        const uint16_t* xs2 = prm.sl[src][2];
         uint16_t* o0 = prm.sl[dst][0];
         uint16_t* o1 = prm.sl[dst][1];
+        uint16_t* o2 = prm.sl[dst][2];
         const size_t P = prm.pitch;
         for (int t = 0; t < ntiles; ++t, ++tile_epi) {
           const uint32_t tb = tile_epi & 1u;
@@ -308,24 +336,25 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int ch = 0; ch < BM / 32; ++ch) {
               float v0[32], v1[32];
               tmem_ld32(tmem + lane_base + 256u * tb + ch * 32, v0);
-              tmem_ld32(tmem + lane_base + 256u * tb + 128u + ch * 32, v1);
+              if (NS == 2) tmem_ld32(tmem + lane_base + 256u * tb + 128u + ch * 32, v1);
               tmem_ld_wait();
               const int c0 = J * BM + ch * 32;
               float trf = 0.0f, frf = 0.0f;
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
                 const int c = c0 + j;
-                float x = v0[j] + v1[j] * (1.0f / 2048.0f);
+                float x = (NS == 2) ? v0[j] + v1[j] * (1.0f / 2048.0f) : v0[j];
                 if (bit) {
                   const size_t mi = (size_t)(in.row0 + c) * P + r;
-                  x = 2.0f * join_value<kFP16x2>(xs0[mi], xs1[mi], 0) - x;
+                  x = 2.0f * join_value<F>(xs0[mi], xs1[mi], NS == 3 ? xs2[mi] : (uint16_t)0) - x;
                 }
                 if (r <= c) {
                   uint16_t a, b, c2;
-                  split_value_f<kFP16x2>(x, a, b, c2);
+                  split_value_f<F>(x, a, b, c2);
                   const size_t dd = (size_t)(in.row0 + r) * P + c;
                   o0[dd] = a;
                   o1[dd] = b;
+                  if (NS == 3) o2[dd] = c2;
                   if (r == c) {
                     trf += x;
                     frf += x * x;
@@ -334,6 +363,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const size_t mi = (size_t)(in.row0 + c) * P + r;
                     o0[mi] = a;
                     o1[mi] = b;
+                    if (NS == 3) o2[mi] = c2;
                   }
                 }
               }
@@ -376,11 +406,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int fin = st.iter & 1;
       const uint16_t* s0 = prm.sl[fin][0];
       const uint16_t* s1 = prm.sl[fin][1];
+      const uint16_t* s2 = prm.sl[fin][2];
       double* D = prm.D + in.offset;
       for (int idx = threadIdx.x; idx < n * n; idx += THREADS) {
         const int r = idx / n, c = idx - r * n;
         const size_t g = (size_t)(in.row0 + r) * prm.pitch + c;
-        D[idx] = (double)join_value<kFP16x2>(s0[g], s1[g], 0);
+        D[idx] = (double)join_value<F>(s0[g], s1[g], NS == 3 ? s2[g] : (uint16_t)0);
       }
       if (threadIdx.x == 0) {
         if (prm.iters) prm.iters[inst] = st.iter;
@@ -439,27 +470,34 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 
 }  // namespace
 
-size_t smem_bytes() { return SMEM; }
-
 cudaError_t launch(const Params& prm, int grid, cudaStream_t s) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
   if (!enc) return cudaErrorNotSupported;
+  const bool bf = fmt_bf16(prm.fmt);
+  const int ns = fmt_slices(prm.fmt);
   Maps maps;
   memset(&maps, 0, sizeof maps);
   for (int k = 0; k < 2; ++k)
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < ns; ++j) {
       cuuint64_t dims[2] = {(cuuint64_t)prm.pitch, (cuuint64_t)prm.total_rows};
       cuuint64_t strides[1] = {(cuuint64_t)prm.pitch * 2};
       cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
       cuuint32_t estr[2] = {1, 1};
-      if (enc(&maps.m[k][j], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)prm.sl[k][j], dims,
-              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+      if (enc(&maps.m[k][j], bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+              2, (void*)prm.sl[k][j], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     }
-  cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-  batched_kernel<<<grid, THREADS, SMEM, s>>>(maps, prm);
+  if (bf) {
+    cudaFuncSetAttribute(batched_kernel<kBF16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         BCfg<kBF16x3>::SMEM);
+    batched_kernel<kBF16x3><<<grid, THREADS, BCfg<kBF16x3>::SMEM, s>>>(maps, prm);
+  } else {
+    cudaFuncSetAttribute(batched_kernel<kFP16x2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         BCfg<kFP16x2>::SMEM);
+    batched_kernel<kFP16x2><<<grid, THREADS, BCfg<kFP16x2>::SMEM, s>>>(maps, prm);
+  }
   return cudaGetLastError();
 }
 

@@ -34,7 +34,8 @@ struct Params {
   double tol;
   const double* H;        // packed inputs
   double* D;              // packed outputs
-  uint16_t* sl[2][2];     // [set][slice] tall FP16x2 slice matrices, total_rows x pitch
+  int32_t fmt;            // SliceFmt: kFP16x2 or kBF16x3
+  uint16_t* sl[2][3];     // [set][slice] tall slice matrices, total_rows x pitch
   // learned-sequence inputs/outputs (all optional)
   const double* bounds_in;               // [batch][2] emin, emax (NaN = Gershgorin)
   const unsigned long long* pred_bits;   // [batch][4]
@@ -48,7 +49,6 @@ struct Params {
   InstanceInfo* info;     // [batch] optional details
 };
 
-size_t smem_bytes();
 cudaError_t launch(const Params& prm, int grid, cudaStream_t s);
 
 }  // namespace batched

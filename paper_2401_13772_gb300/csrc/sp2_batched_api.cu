@@ -14,6 +14,7 @@
 #include "progress_sp2.h"
 #include "sp2_batched.h"
 #include "sp2_launch.h"
+#include "sp2_slices.cuh"
 
 namespace {
 
@@ -24,7 +25,8 @@ using sp2::batched::Params;
 struct BatchWs {
   cudaStream_t cap = nullptr;
   // device buffers
-  uint16_t* sl[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  uint16_t* sl[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int nslices = 0;
   size_t slice_elems = 0;
   Instance* inst = nullptr;
   int32_t* order = nullptr;
@@ -54,11 +56,12 @@ progress_status_t bcuda(cudaError_t e, const char* where) {
 
 void free_bufs(BatchWs* w) {
   for (int k = 0; k < 2; ++k)
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < 3; ++j) {
       if (w->sl[k][j]) cudaFree(w->sl[k][j]);
       w->sl[k][j] = nullptr;
     }
   w->slice_elems = 0;
+  w->nslices = 0;
 }
 
 void free_meta(BatchWs* w) {
@@ -126,8 +129,11 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
   if (!h_n || !h_offset || !h_nocc || !dH || !dD)
     return bfail(PROGRESS_EINVAL, "NULL pointer argument");
   if (!(tol >= 0.0)) return bfail(PROGRESS_EINVAL, "tol must be >= 0");
-  if (o.prec != PROGRESS_FP32_SPLIT)
-    return bfail(PROGRESS_EUNSUPPORTED, "the batched solver runs PROGRESS_FP32_SPLIT only");
+  if (o.prec != PROGRESS_FP32_SPLIT && o.prec != PROGRESS_FP32_SPLIT_BF16)
+    return bfail(PROGRESS_EUNSUPPORTED,
+                 "the batched solver runs PROGRESS_FP32_SPLIT or PROGRESS_FP32_SPLIT_BF16 only");
+  const int fmt = o.prec == PROGRESS_FP32_SPLIT_BF16 ? sp2::kBF16x3 : sp2::kFP16x2;
+  const int nsl = sp2::fmt_slices(fmt);
   if (o.rule != PROGRESS_RULE_NEARER && o.rule != PROGRESS_RULE_PAPER)
     return bfail(PROGRESS_EINVAL, "unknown branch rule");
   if (o.maxiter < 0 || o.maxiter > 250) return bfail(PROGRESS_EINVAL, "maxiter must be in [0, 250]");
@@ -175,21 +181,24 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
   }
   // workspace
   const size_t need = (size_t)rows * pitch;
-  if (need > w->slice_elems || batch > w->cap_batch) {
+  if (need > w->slice_elems || nsl > w->nslices || batch > w->cap_batch) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bcuda(e, "cudaStreamSynchronize");
     drop_graph(w);
   }
-  if (need > w->slice_elems) {
+  if (need > w->slice_elems || nsl > w->nslices) {
+    const size_t alloc = need > w->slice_elems ? need : w->slice_elems;
+    const int ns = nsl > w->nslices ? nsl : w->nslices;
     free_bufs(w);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k)
-      for (int j = 0; j < 2 && e == cudaSuccess; ++j)
-        e = cudaMalloc(&w->sl[k][j], need * sizeof(uint16_t));
+      for (int j = 0; j < ns && e == cudaSuccess; ++j)
+        e = cudaMalloc(&w->sl[k][j], alloc * sizeof(uint16_t));
     if (e != cudaSuccess) {
       free_bufs(w);
       return bcuda(e, "batched slice allocation");
     }
-    w->slice_elems = need;
+    w->slice_elems = alloc;
+    w->nslices = ns;
   }
   if (batch > w->cap_batch) {
     free_meta(w);
@@ -222,8 +231,9 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
   prm.tol = tol;
   prm.H = dH;
   prm.D = dD;
+  prm.fmt = fmt;
   for (int k = 0; k < 2; ++k)
-    for (int j = 0; j < 2; ++j) prm.sl[k][j] = w->sl[k][j];
+    for (int j = 0; j < 3; ++j) prm.sl[k][j] = w->sl[k][j];
   prm.iters = d_iters;
   prm.status = d_status;
   prm.info = w->info;

@@ -64,8 +64,9 @@ def trace_hd(batch, D):
 
 
 def batched_solve(batch, nocc, tol=1e-10, bounds=None, pred_bits=None, pred_len=None,
-                  judge_delta=0.0, maxiter=100):
-    """Batched FP32-split SP2 with optional learned inputs.
+                  judge_delta=0.0, maxiter=100, prec="fp32_split_bf16"):
+    """Batched split-precision SP2 with optional learned inputs (bf16 slices by
+    default: their exponent range keeps runs with nocc << n intact).
 
     Returns a dict of CUDA tensors: D (packed), iters, status, bits [B,4]
     (uint64 stored as int64), bounds [B,2], fallback."""
@@ -87,7 +88,7 @@ def batched_solve(batch, nocc, tol=1e-10, bounds=None, pred_bits=None, pred_len=
     ex.d_bits_out = bits.data_ptr()
     ex.d_bounds_out = bnd.data_ptr()
     ex.d_fallback = fb.data_ptr()
-    o = make_opts(prec="fp32_split", maxiter=maxiter)
+    o = make_opts(prec=prec, maxiter=maxiter)
     n = np.ascontiguousarray(batch["n"], dtype=np.int32)
     off = np.ascontiguousarray(batch["offsets"], dtype=np.int64)
     check(load().progress_sp2_batched_ex(

