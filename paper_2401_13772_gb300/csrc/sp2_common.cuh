@@ -138,20 +138,22 @@ __device__ inline void decide(State* st) {
     }
     if (phase == kPhaseSplit && k > 0) {
       // Low precision stops helping once the idempotency error sits on its
-      // round-off floor. Plateaus of the error above 0.01 are not that floor:
-      // each eigenvalue still between 0.01 and 0.99 adds at least 0.0099, and
-      // SP2 holds the last few pairs around the gap near 0.5 for many steps
-      // while it separates them (one pair at 0.5 alone contributes 0.5, and
-      // the first steps oscillate far above 1). So: two steps without a 0.1 %
-      // improvement below 0.01, or eight below 0.1.
+      // round-off floor, about n u for split operands (u ~ 2^-22). Above that
+      // level the error is not a floor: SP2 can hold it on long plateaus or
+      // oscillate (each eigenvalue still inside (0.01, 0.99) adds ~0.01 or
+      // more; with few occupied states the error doubles for several steps
+      // between drops). So: two steps without a 0.1 % improvement while below
+      // 16 n 2^-22.
+      const double floor_thr = 16.0 * n * 2.384185791015625e-07;
       if (idem < st->best_split_idem * 0.999) {
         st->best_split_idem = idem;
         st->split_stall = 0;
       } else {
         ++st->split_stall;
-        if ((st->split_stall >= 2 && idem < 0.01) || (st->split_stall >= 8 && idem < 0.1))
-          stalled = true;
+        if (st->split_stall >= 2 && idem < floor_thr) stalled = true;
       }
+      // MIXED: leave room for the FP64 refinement before maxiter.
+      if (st->prec != PROGRESS_FP32_SPLIT && k >= st->maxiter - 10) stalled = true;
     }
     if (stalled && st->prec != PROGRESS_FP32_SPLIT) phase = kPhaseRefine;  // MIXED
   }
