@@ -269,13 +269,27 @@ def label_batch(batch, nocc, margin, kmax, tol=1e-10):
             "label_iters": run["iters"]}
 
 
-def solve_learned(pred, batch, nocc, emin, emax, margin, judge_delta, tol=1e-10):
-    """Batched solve with predicted bounds and branch bits, judged by the trace rule."""
+def confident_prefix(logits, tau):
+    """Per row, the number of leading branch logits with |logit| >= tau: only
+    that prefix of the sequence is predicted; later branches are left to the
+    trace rule (no prediction to judge)."""
     import torch
+    conf = (logits.abs() >= tau).to(torch.int32)
+    # length of the leading run of ones
+    run = torch.cumprod(conf, dim=1)
+    return run.sum(dim=1).to(torch.int32).contiguous()
+
+
+def solve_learned(pred, batch, nocc, emin, emax, margin, judge_delta, tau=2.0, tol=1e-10):
+    """Batched solve with predicted bounds and the confident prefix of the
+    predicted branch sequence, judged by the trace rule."""
     X = features(batch)
     Y = pred.predict(X)
     bounds = predicted_bounds(Y, emin, emax, margin)
-    bits = array_to_bits_tensor((Y[:, N_BOUNDS:] > 0).float())
-    plen = torch.full((Y.shape[0],), pred.kmax, dtype=torch.int32, device=Y.device)
-    return batched_solve(batch, nocc, tol, bounds=bounds, pred_bits=bits, pred_len=plen,
-                         judge_delta=judge_delta)
+    logits = Y[:, N_BOUNDS:]
+    bits = array_to_bits_tensor((logits > 0).float())
+    plen = confident_prefix(logits, tau)
+    out = batched_solve(batch, nocc, tol, bounds=bounds, pred_bits=bits, pred_len=plen,
+                        judge_delta=judge_delta)
+    out["pred_len"] = plen
+    return out
