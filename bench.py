@@ -62,6 +62,16 @@ def parse_args():
                     help="skip the torch-side invariants of D (profiling runs)")
     ap.add_argument("--loop-mode", type=int, default=0,
                     help="0: device-driven WHILE graph; 1: plain launches (profilers)")
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "learned"],
+                    help="dense: one N = 4096 cube solve per step (headline); batched: 4000 "
+                         "parts of 64..768 orbitals per step; learned: predictor training "
+                         "and evaluation")
+    ap.add_argument("--batch", type=int, default=4000)
+    ap.add_argument("--batch-prec", default="fp32_split",
+                    choices=["fp32_split", "fp32_split_bf16"])
+    ap.add_argument("--train-count", type=int, default=20000)
+    ap.add_argument("--eval-count", type=int, default=1000)
+    ap.add_argument("--eval-sites", type=int, default=512)
     return ap.parse_args()
 
 
@@ -203,10 +213,209 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 
+def run_batched(args):
+    """Batched workload: `--batch` cube parts of U{16..192} sites (n = 64..768),
+    Nocc = n/2, one persistent launch per step."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2401_13772_gb300 as pkg
+    from paper_2401_13772_gb300.build import build
+    from workloads import batch_packed, batch_sizes
+    sites = batch_sizes(args.batch, 0)
+    packed, n, offsets, nocc = batch_packed(sites, 1000)
+    build()
+    dev = torch.device("cuda", 0)
+    Hh = torch.from_numpy(packed).pin_memory()
+    H = Hh.to(dev)
+    D = torch.empty_like(H)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, args.warmup)):
+        D, iters, status = pkg.sp2_batched(H, n, offsets, nocc, 1e-10, D_packed=D,
+                                           prec=args.batch_prec)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+    clocks = ClockSampler()
+    clocks.start()
+    for i in range(K):
+        ev[2 * i].record(stream)
+        pkg.sp2_batched(H, n, offsets, nocc, 1e-10, D_packed=D, prec=args.batch_prec)
+        ev[2 * i + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(K)) / K / 1e3
+    it = iters.cpu().numpy()
+    st = status.cpu().numpy()
+    nn = n.astype(np.float64)
+    flops = float(np.sum(it * nn * nn * (nn + 1)))
+    peaks, src = load_peaks()
+    peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
+    ach = flops / sec / 1e12
+    # a loop of plain per-instance solves (dense FP32-split API), subsample
+    sub = np.linspace(0, args.batch - 1, 100).astype(int)
+    mats = [torch.from_numpy(packed[offsets[i]:offsets[i] + int(n[i]) ** 2].reshape(
+        int(n[i]), int(n[i]))).to(dev) for i in sub]
+    for m_, i in zip(mats[:3], sub[:3]):
+        pkg.sp2_dense_ex(m_, int(nocc[i]), 1e-10, prec="fp32_split")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for m_, i in zip(mats, sub):
+        pkg.sp2_dense_ex(m_, int(nocc[i]), 1e-10, info=False, prec="fp32_split")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_sec = e0.elapsed_time(e1) / 1e3 * args.batch / len(sub)
+    # accuracy on a sample against the oracle
+    Dh = D.cpu().numpy()
+    errs = []
+    for i in sub[::12]:
+        k = int(n[i])
+        Hi = packed[offsets[i]:offsets[i] + k * k].reshape(k, k)
+        ref = oracle.sp2_plain(Hi, int(nocc[i]), 1e-10)
+        errs.append(float(np.abs(Dh[offsets[i]:offsets[i] + k * k].reshape(k, k) -
+                              ref["D"]).max()))
+    # the oracle on a bounded sample of the batch, scaled to the whole batch
+    t0 = time.perf_counter()
+    for i in sub[:20]:
+        k = int(n[i])
+        oracle.sp2_plain(packed[offsets[i]:offsets[i] + k * k].reshape(k, k), int(nocc[i]),
+                         1e-10)
+    cpu_sec = (time.perf_counter() - t0) * args.batch / 20
+    # end to end through the C ABI with host buffers
+    Dh_pin = torch.empty_like(Hh).pin_memory()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    H.copy_(Hh, non_blocking=True)
+    pkg.sp2_batched(H, n, offsets, nocc, 1e-10, D_packed=D, prec=args.batch_prec)
+    Dh_pin.copy_(D, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_sec = e0.elapsed_time(e1) / 1e3
+    line = {"metric": METRIC, "value": args.batch / sec, "unit": UNIT, "n_gpus": 1,
+            "steps": K, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ("f16x2 split, f32 accumulate" if args.batch_prec == "fp32_split"
+                      else "bf16x3 split, f32 accumulate"),
+            "data": "synthetic",
+            "config": {"workload": f"{args.batch} random-cube parts, U{{16..192}} sites x 4 "
+                                   f"orbitals (n = 64..768), Nocc = n/2, seeds 1000+i",
+                       "prec": args.batch_prec, "tol": 1e-10,
+                       "l2": "inputs (about 7 GB) far larger than L2"},
+            "iters_mean": float(it.mean()), "status_ok": int((st == 0).sum()),
+            "tflops_algorithmic": ach,
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "traffic": None, "kernel": "batched_kernel",
+                         "peak_source": f"fp16/bf16 dense, {src} burst",
+                         "flops_per_launch": flops, "avg_launch_ms": sec * 1e3},
+            "loop_baseline": {"value": args.batch / loop_sec, "unit": UNIT,
+                              "what": "per-instance dense FP32-split solves in a loop "
+                                      "(100-instance subsample, scaled)"},
+            "d_check": {"max_abs_err_vs_oracle_sample": max(errs), "sample": len(errs)},
+            "cpu_baseline": {"value": args.batch / cpu_sec, "unit": UNIT,
+                             "cores": cpu_cores(), "kind": "oracle",
+                             "sample": "20 instances of the batch (plain FP64 SP2, numpy), "
+                                       "scaled to the batch"},
+            "e2e": {"value": args.batch / e2e_sec, "unit": UNIT,
+                    "h2d_bytes_per_step": int(packed.nbytes),
+                    "d2h_bytes_per_step": int(packed.nbytes)},
+            "gpu_launches": K, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args):
+    """Learned workload: train the predictor on `--train-count` cube instances
+    (n = 256..2048 in steps of 4, seeds 10000+i) with SP2-derived labels, then
+    evaluate on `--eval-count` fresh instances of `--eval-sites` sites (seeds
+    50000+i): products per solve, fallback rate and batched solves/s with and
+    without the predictions."""
+    import numpy as np
+    import torch
+    from paper_2401_13772_gb300 import learned as L
+    from paper_2401_13772_gb300.build import build
+    from workloads import batch_packed
+    build()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(0)
+    train_sites = rng.integers(64, 513, size=args.train_count)
+    margin, kmax = 0.01, 80
+    Xs, Ts, Ms = [], [], []
+    t0 = time.perf_counter()
+    chunk = 500
+    for c0 in range(0, args.train_count, chunk):
+        s = train_sites[c0:c0 + chunk]
+        packed, n, offsets, nocc = batch_packed(s, 10000 + c0)
+        b = {"H": torch.from_numpy(packed).to(dev), "n": n, "offsets": offsets,
+             "d_n": torch.from_numpy(n).to(dev), "d_off": torch.from_numpy(offsets).to(dev)}
+        lab = L.label_batch(b, nocc, margin, kmax)
+        Xs.append(lab["X"])
+        Ts.append(lab["T"])
+        Ms.append(lab["M"])
+        del b, lab
+    t_label = time.perf_counter() - t0
+    X, T, M = torch.cat(Xs), torch.cat(Ts), torch.cat(Ms)
+    P = L.Predictor(hidden=128, kmax=kmax, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = P.fit(X, T, M, epochs=60, batch=512, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    packed, n, offsets, nocc = batch_packed(np.full(args.eval_count, args.eval_sites), 50000)
+    ev = {"H": torch.from_numpy(packed).to(dev), "n": n, "offsets": offsets,
+          "d_n": torch.from_numpy(n).to(dev), "d_off": torch.from_numpy(offsets).to(dev)}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    plain, t_plain = timed(lambda: L.batched_solve(ev, nocc))
+    g0, g1 = plain["bounds"][:, 0], plain["bounds"][:, 1]
+
+    def learned_solve():
+        Y = P.predict(L.features(ev))
+        return L.batched_solve(ev, nocc, bounds=L.predicted_bounds(Y, g0, g1, margin))
+    lb, t_lb = timed(learned_solve)
+    lj, t_lj = timed(lambda: L.solve_learned(P, ev, nocc, g0, g1, margin, judge_delta=0.5))
+    line = {"metric": METRIC, "value": args.eval_count / t_lb, "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": t_lb * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 split, f32 accumulate",
+            "data": "synthetic",
+            "config": {"workload": f"learned bounds/branches: train {args.train_count} cube "
+                                   f"instances (n 256..2048), eval {args.eval_count} x "
+                                   f"n = {4 * args.eval_sites}",
+                       "hidden": 128, "kmax": kmax, "margin": margin, "judge_delta": 0.5},
+            "plain": {"solves_per_s": args.eval_count / t_plain,
+                      "products_mean": plain["iters"].double().mean().item()},
+            "predicted_bounds": {"solves_per_s": args.eval_count / t_lb,
+                                 "products_mean": lb["iters"].double().mean().item(),
+                                 "fallback_rate": lb["fallback"].double().mean().item()},
+            "bounds_and_branches": {"solves_per_s": args.eval_count / t_lj,
+                                    "products_mean": lj["iters"].double().mean().item(),
+                                    "fallback_rate": lj["fallback"].double().mean().item(),
+                                    "predicted_prefix_mean":
+                                        lj["pred_len"].double().mean().item()},
+            "training": {"label_s": t_label, "train_s": t_train, "loss_first": losses[0],
+                         "loss_last": losses[-1], "samples": args.train_count}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "learned":
+        run_learned(args)
         return
     import numpy as np
     import torch

@@ -14,6 +14,7 @@ from .hamiltonians import (  # noqa: F401
     cube_geometry,
     batch_sizes,
     batch_instance,
+    batch_packed,
     CUBE_DENSITY,
     CUBE_CUTOFF,
 )

@@ -103,3 +103,54 @@ def batch_sizes(count: int = 4000, seed: int = 0, lo_sites: int = 16,
 def batch_instance(index: int, sites: int, base_seed: int = 1000):
     """Instance ``index`` of a batch: a cube Hamiltonian with seed base+index."""
     return cube_hamiltonian(int(sites), base_seed + int(index))
+
+
+def _fill_batch(args):
+    """Worker: write instances [lo, hi) of a batch into a file-backed buffer."""
+    path, total, sites, offsets, lo, hi, base_seed = args
+    buf = np.memmap(path, dtype=np.float64, mode="r+", shape=(total,))
+    for i in range(lo, hi):
+        H, _ = cube_hamiltonian(int(sites[i]), base_seed + i)
+        n = H.shape[0]
+        buf[offsets[i]:offsets[i] + n * n] = H.ravel()
+    buf.flush()
+    del buf
+    return hi - lo
+
+
+def batch_packed(sites, base_seed=1000, workers=None):
+    """All instances of a batch packed row-major into one FP64 vector.
+
+    Instance i is cube_hamiltonian(sites[i], base_seed + i); returns
+    (packed, n, offsets, nocc). Generation runs in `workers` processes
+    (spawned, so it is safe before or after CUDA initialisation) writing into
+    a temporary file-backed buffer."""
+    import multiprocessing as mp
+    import os
+    import tempfile
+    sites = np.asarray(sites, dtype=np.int64)
+    n = (ORBITALS_PER_SITE * sites).astype(np.int32)
+    sizes = n.astype(np.int64) ** 2
+    offsets = np.zeros(len(n), dtype=np.int64)
+    if len(n) > 1:
+        offsets[1:] = np.cumsum(sizes)[:-1]
+    total = int(sizes.sum())
+    if workers is None:
+        workers = min(16, os.cpu_count() or 1)
+    fd, path = tempfile.mkstemp(suffix=".f64")
+    os.close(fd)
+    try:
+        np.memmap(path, dtype=np.float64, mode="w+", shape=(max(total, 1),)).flush()
+        chunks = np.linspace(0, len(n), max(1, workers * 4) + 1).astype(int)
+        jobs = [(path, total, sites, offsets, int(a), int(b), base_seed)
+                for a, b in zip(chunks[:-1], chunks[1:]) if b > a]
+        if workers > 1 and len(jobs) > 1:
+            with mp.get_context("spawn").Pool(workers) as pool:
+                pool.map(_fill_batch, jobs)
+        else:
+            for j in jobs:
+                _fill_batch(j)
+        packed = np.array(np.memmap(path, dtype=np.float64, mode="r", shape=(total,)))
+    finally:
+        os.unlink(path)
+    return packed, n, offsets, (n // 2).astype(np.int32)
