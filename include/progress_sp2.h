@@ -197,7 +197,10 @@ typedef struct {
   double* d_bounds_out;        /* device [batch][2]: bounds used, or NULL */
   int32_t* d_fallback;         /* device [batch]: 1 if the instance reverted to the plain
                                   path (Gershgorin bounds, trace rule), or NULL */
-  int32_t reserved[8];         /* must be zero */
+  int32_t* d_products;         /* device [batch]: products executed in total, including a
+                                  rejected predicted run (d_iters counts the final run only),
+                                  or NULL */
+  int32_t reserved[6];         /* must be zero */
 } progress_batch_ex_t;
 
 /*

@@ -49,7 +49,8 @@ class BatchEx(ctypes.Structure):
     _fields_ = [("d_bounds", ctypes.c_void_p), ("d_pred_bits", ctypes.c_void_p),
                 ("d_pred_len", ctypes.c_void_p), ("judge_delta", ctypes.c_double),
                 ("d_bits_out", ctypes.c_void_p), ("d_bounds_out", ctypes.c_void_p),
-                ("d_fallback", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 8)]
+                ("d_fallback", ctypes.c_void_p), ("d_products", ctypes.c_void_p),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 # symbol -> (restype, argtypes); every function declared in include/progress_sp2.h

@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // diverges) is restarted once on the plain path.
     bool predicted = prm.bounds_in != nullptr || prm.pred_bits != nullptr;
     bool fell_back = false;
+    int wasted = 0;  // products of a rejected predicted run
   restart:
 
     // ---- set-up: state, Gershgorin bounds, X0 (all threads)
@@ -397,6 +398,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                                st.status == PROGRESS_ENOCONV)) {
       predicted = false;
       fell_back = true;
+      wasted = st.iter;
       __syncthreads();
       goto restart;
     }
@@ -416,6 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (threadIdx.x == 0) {
         if (prm.iters) prm.iters[inst] = st.iter;
         if (prm.fallback) prm.fallback[inst] = fell_back ? 1 : 0;
+        if (prm.products) prm.products[inst] = st.iter + wasted;
         if (prm.bits_out)
           for (int b = 0; b < 4; ++b) prm.bits_out[4 * inst + b] = st.bits[b];
         if (prm.bounds_out) {

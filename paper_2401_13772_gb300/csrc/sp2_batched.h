@@ -44,6 +44,7 @@ struct Params {
   unsigned long long* bits_out;          // [batch][4]
   double* bounds_out;                    // [batch][2]
   int32_t* fallback;                     // [batch]
+  int32_t* products;                     // [batch] products including a rejected attempt
   int32_t* iters;         // [batch] products per instance (may be null)
   int32_t* status;        // [batch] progress_status_t per instance (may be null)
   InstanceInfo* info;     // [batch] optional details

@@ -245,6 +245,7 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
     prm.bits_out = reinterpret_cast<unsigned long long*>(ex->d_bits_out);
     prm.bounds_out = ex->d_bounds_out;
     prm.fallback = ex->d_fallback;
+    prm.products = ex->d_products;
   }
 
   const bool same_layout = w->have_last && w->last_inst.size() == inst.size() &&

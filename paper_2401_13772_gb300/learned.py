@@ -80,6 +80,7 @@ def batched_solve(batch, nocc, tol=1e-10, bounds=None, pred_bits=None, pred_len=
     bits = torch.zeros((B, 4), dtype=torch.int64, device=dev)
     bnd = torch.zeros((B, 2), dtype=torch.float64, device=dev)
     fb = torch.zeros(B, dtype=torch.int32, device=dev)
+    prod = torch.zeros(B, dtype=torch.int32, device=dev)
     ex = _lib.BatchEx()
     ex.d_bounds = bounds.data_ptr() if bounds is not None else None
     ex.d_pred_bits = pred_bits.data_ptr() if pred_bits is not None else None
@@ -88,6 +89,7 @@ def batched_solve(batch, nocc, tol=1e-10, bounds=None, pred_bits=None, pred_len=
     ex.d_bits_out = bits.data_ptr()
     ex.d_bounds_out = bnd.data_ptr()
     ex.d_fallback = fb.data_ptr()
+    ex.d_products = prod.data_ptr()
     o = make_opts(prec=prec, maxiter=maxiter)
     n = np.ascontiguousarray(batch["n"], dtype=np.int32)
     off = np.ascontiguousarray(batch["offsets"], dtype=np.int64)
@@ -96,7 +98,7 @@ def batched_solve(batch, nocc, tol=1e-10, bounds=None, pred_bits=None, pred_len=
         ctypes.c_void_p(nocc.ctypes.data), _p(batch["H"]), float(tol), _p(D), _p(iters),
         _p(status), ctypes.byref(o), ctypes.byref(ex), _stream_ptr()))
     return {"D": D, "iters": iters, "status": status, "bits": bits, "bounds": bnd,
-            "fallback": fb}
+            "fallback": fb, "products": prod}
 
 
 def extremal_eigenvalues(batch, tol=1e-10):
@@ -256,17 +258,32 @@ def make_targets(u_min, u_max, bits, iters, kmax):
 
 
 def label_batch(batch, nocc, margin, kmax, tol=1e-10):
-    """Features, targets and masks of one packed batch (SP2-derived labels)."""
+    """Features and bound targets of one packed batch (SP2-derived labels);
+    the branch targets are filled by ``branch_labels`` once bounds can be
+    predicted."""
     feat = features(batch)
     e1, eN, emin, emax = extremal_eigenvalues(batch, tol)
     u_min, u_max = bound_fractions(e1, eN, emin, emax)
-    w = emax - emin
     import torch
-    lab_bounds = torch.stack([e1 - margin * w, eN + margin * w], dim=1).contiguous()
-    run = batched_solve(batch, nocc, tol, bounds=lab_bounds)
-    T, M = make_targets(u_min, u_max, run["bits"], run["iters"], kmax)
-    return {"X": feat, "T": T, "M": M, "emin": emin, "emax": emax, "eps1": e1, "epsN": eN,
-            "label_iters": run["iters"]}
+    iters0 = torch.zeros_like(u_min, dtype=torch.int32)
+    bits0 = torch.zeros((u_min.shape[0], 4), dtype=torch.int64, device=u_min.device)
+    T, M = make_targets(u_min, u_max, bits0, iters0, kmax)
+    return {"X": feat, "T": T, "M": M, "emin": emin, "emax": emax, "eps1": e1, "epsN": eN}
+
+
+def branch_labels(pred, batch, nocc, lab, margin, tol=1e-10):
+    """Branch targets consistent with inference: the bits of an SP2 run whose
+    X0 uses the bounds ``pred`` predicts (widened by margin), and bound
+    targets replaced by ``pred``'s own outputs so that further training keeps
+    those bounds while it learns the branches."""
+    Y = pred.predict(lab["X"])
+    bounds = predicted_bounds(Y, lab["emin"], lab["emax"], margin)
+    run = batched_solve(batch, nocc, tol, bounds=bounds)
+    ok = run["fallback"] == 0
+    kmax = lab["T"].shape[1] - N_BOUNDS
+    T, M = make_targets(Y[:, 0].double(), Y[:, 1].double(), run["bits"], run["iters"], kmax)
+    M[~ok, N_BOUNDS:] = 0.0  # a run that failed gives no branch labels
+    return T, M
 
 
 def confident_prefix(logits, tau):
