@@ -58,10 +58,13 @@ typedef enum {
   PROGRESS_MIXED_FP16 = 2,  /* fp64_prefix FP64 products, then fp16 hi+lo split products, then
                                FP64 refinement products until idempotent in FP64 */
   PROGRESS_MIXED_BF16 = 3,  /* as MIXED_FP16 with bf16 hi+mid+lo (3-way) splits */
-  PROGRESS_FP32_SPLIT_BF16 = 4 /* as FP32_SPLIT with bf16 hi+mid+lo splits: six products
+  PROGRESS_FP32_SPLIT_BF16 = 4, /* as FP32_SPLIT with bf16 hi+mid+lo splits: six products
                                instead of three, but FP32's exponent range (fp16 slices
                                flush entries below ~6e-8, which runs with nocc << n reach
                                by repeated squaring) */
+  PROGRESS_DF64 = 5         /* every product in double-float (pairs of FP32, ~47 bits) on
+                               the FP32 pipe: FP64-class accuracy, several times the FP64
+                               pipe's rate on this part */
 } progress_prec_t;
 
 typedef enum {
@@ -84,7 +87,10 @@ typedef struct {
   void* loop_events[2]; /* optional cudaEvent_t pair (or NULL) recorded on the stream
                            right before and right after the product loop, so a
                            caller can time the products alone */
-  int32_t reserved[4];  /* must be zero */
+  int32_t fp64_impl;    /* MIXED_*: arithmetic of the FP64-accurate products (prefix and
+                           refinement): 0 = double-float on the FP32 pipe (default),
+                           1 = native FP64 (DMMA) */
+  int32_t reserved[3];  /* must be zero */
 } progress_opts_t;
 
 /* Result of one solve, read back from the device by the calls that take it. */

@@ -18,7 +18,7 @@ import math
 
 from . import _lib
 from ._lib import (  # noqa: F401
-    FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16, FP32_SPLIT_BF16, RULE_NEARER, RULE_PAPER,
+    FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16, FP32_SPLIT_BF16, DF64, RULE_NEARER, RULE_PAPER,
     Info, Opts, ProgressError, load, check,
 )
 
@@ -27,7 +27,7 @@ __all__ = ["gershgorin_bounds", "sp2_dense", "sp2_dense_ex", "release", "load",
            "PREC_NAMES", "ProgressError"]
 
 PREC_NAMES = {"fp64": FP64, "fp32_split": FP32_SPLIT, "mixed_fp16": MIXED_FP16,
-              "mixed_bf16": MIXED_BF16, "fp32_split_bf16": FP32_SPLIT_BF16}
+              "mixed_bf16": MIXED_BF16, "fp32_split_bf16": FP32_SPLIT_BF16, "df64": DF64}
 RULE_NAMES = {"nearer": RULE_NEARER, "paper": RULE_PAPER}
 
 
@@ -63,7 +63,7 @@ def gershgorin_bounds(H, out=None, stream=None):
 
 
 def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None, emax=None,
-              loop_mode=0, loop_events=None, slice_fixed=0):
+              loop_mode=0, loop_events=None, slice_fixed=0, fp64_impl=0):
     o = Opts()
     load().progress_opts_default(ctypes.byref(o))
     o.prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
@@ -74,6 +74,7 @@ def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None
     o.emax = math.nan if emax is None else float(emax)
     o.loop_mode = int(loop_mode)
     o.slice_fixed = int(slice_fixed)
+    o.fp64_impl = int(fp64_impl)
     if loop_events is not None:
         # torch.cuda.Event pair, already created (recorded once)
         o.loop_events[0] = loop_events[0].cuda_event

@@ -17,7 +17,7 @@ STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOCONV: "ENOCONV", EBOUNDS: "EBOUND
                 ECUDA: "ECUDA", ENOMEM: "ENOMEM", ETIMEOUT: "ETIMEOUT",
                 EUNSUPPORTED: "EUNSUPPORTED"}
 
-FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16, FP32_SPLIT_BF16 = range(5)
+FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16, FP32_SPLIT_BF16, DF64 = range(6)
 RULE_NEARER, RULE_PAPER = 0, 1
 
 
@@ -26,7 +26,8 @@ class Opts(ctypes.Structure):
                 ("fp64_prefix", ctypes.c_int32), ("maxiter", ctypes.c_int32),
                 ("emin", ctypes.c_double), ("emax", ctypes.c_double),
                 ("loop_mode", ctypes.c_int32), ("slice_fixed", ctypes.c_int32),
-                ("loop_events", ctypes.c_void_p * 2), ("reserved", ctypes.c_int32 * 4)]
+                ("loop_events", ctypes.c_void_p * 2), ("fp64_impl", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class Info(ctypes.Structure):

@@ -50,7 +50,7 @@ struct Workspace {
   // cached loop graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int g_ld = -1, g_prec = -1, g_fmt = -1;
+  int g_ld = -1, g_prec = -1, g_fmt = -1, g_df = -1;
 };
 
 std::mutex g_mu;
@@ -61,7 +61,7 @@ void free_graph(Workspace* w) {
   if (w->graph) cudaGraphDestroy(w->graph);
   w->exec = nullptr;
   w->graph = nullptr;
-  w->g_ld = w->g_prec = w->g_fmt = -1;
+  w->g_ld = w->g_prec = w->g_fmt = w->g_df = -1;
 }
 
 void free_matrices(Workspace* w) {
@@ -135,6 +135,7 @@ progress_status_t ensure_buffers(Workspace* w, int ld, bool need_x64, int nslice
       e = cudaMalloc(&w->buf.sl[k][i], elems * sizeof(uint16_t));
   }
   int maxp = sp2::fp64_tile_count(new_ld);
+  if (sp2::df64_tile_count(new_ld) > maxp) maxp = sp2::df64_tile_count(new_ld);
   const int sp = sp2::split_tile_count(new_ld);
   if (sp > maxp) maxp = sp;
   if (maxp < 152 * 8) maxp = 152 * 8;
@@ -161,15 +162,20 @@ int slice_fmt_of(int prec, int fixed) {
 // Queue the product steps of one loop iteration on `s`.
 progress_status_t queue_steps(Workspace* w, const sp2::SolveParams& p, unsigned long long cond,
                               cudaStream_t s) {
-  if (p.prec == PROGRESS_FP64 || is_mixed(p.prec))
-    CK(sp2::launch_square_fp64(w->buf, p.ld, p.slice_fmt, cond, s), "square_fp64 launch");
+  if (p.prec == PROGRESS_FP64 || is_mixed(p.prec)) {
+    if (p.df64)
+      CK(sp2::launch_square_df64(w->buf, p.ld, p.slice_fmt, cond, s), "square_df64 launch");
+    else
+      CK(sp2::launch_square_fp64(w->buf, p.ld, p.slice_fmt, cond, s), "square_fp64 launch");
+  }
   if (p.prec != PROGRESS_FP64)
     CK(sp2::launch_square_split(w->buf, p, cond, s), "square_split launch");
   return PROGRESS_OK;
 }
 
 progress_status_t build_graph(Workspace* w, const sp2::SolveParams& p) {
-  if (w->exec && w->g_ld == p.ld && w->g_prec == p.prec && w->g_fmt == p.slice_fmt)
+  if (w->exec && w->g_ld == p.ld && w->g_prec == p.prec && w->g_fmt == p.slice_fmt &&
+      w->g_df == p.df64)
     return PROGRESS_OK;
   free_graph(w);
   cudaGraph_t g = nullptr;
@@ -216,6 +222,7 @@ progress_status_t build_graph(Workspace* w, const sp2::SolveParams& p) {
   w->g_ld = p.ld;
   w->g_prec = p.prec;
   w->g_fmt = p.slice_fmt;
+  w->g_df = p.df64;
   return PROGRESS_OK;
 }
 
@@ -306,8 +313,15 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   if (n < 0 || n > (1 << 16)) return fail(PROGRESS_EINVAL, "n must be in [0, 65536]");
   if (nocc < 0 || nocc > n) return fail(PROGRESS_EINVAL, "nocc must be in [0, n]");
   if (!(tol >= 0.0)) return fail(PROGRESS_EINVAL, "tol must be >= 0");
-  if (o.prec < PROGRESS_FP64 || o.prec > PROGRESS_FP32_SPLIT_BF16)
+  if (o.prec < PROGRESS_FP64 || o.prec > PROGRESS_DF64)
     return fail(PROGRESS_EINVAL, "unknown precision mode");
+  if (o.fp64_impl != 0 && o.fp64_impl != 1) return fail(PROGRESS_EINVAL, "fp64_impl must be 0 or 1");
+  // double-float FP64-accurate products: the DF64 mode, and the MIXED modes
+  // unless native FP64 is asked for
+  const int df64 = (o.prec == PROGRESS_DF64 ||
+                    ((o.prec == PROGRESS_MIXED_FP16 || o.prec == PROGRESS_MIXED_BF16) &&
+                     o.fp64_impl == 0)) ? 1 : 0;
+  if (o.prec == PROGRESS_DF64) o.prec = PROGRESS_FP64;
   // the all-split bf16 mode is the all-split mode with bf16 slices
   const bool split_bf16 = o.prec == PROGRESS_FP32_SPLIT_BF16;
   if (split_bf16) o.prec = PROGRESS_FP32_SPLIT;
@@ -357,6 +371,7 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   p.prec = o.prec;
   p.fp64_prefix = o.fp64_prefix;
   p.slice_fmt = fmt;
+  p.df64 = df64;
   p.tol = tol;
   p.emin_override = o.emin;
   p.emax_override = o.emax;

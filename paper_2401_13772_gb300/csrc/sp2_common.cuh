@@ -46,6 +46,7 @@ struct State {
   int split_stall;    // consecutive split-phase steps without improvement
   int x_fp64_valid;   // the current iterate X_k is stored in FP64 (buffer k % 2)
   int x_slices_valid; // the current iterate X_k is stored as slices (set k % 2)
+  int df64;           // the FP64 buffers hold double-float planes (hi, lo floats)
   unsigned int ticket;  // CTA arrival counter of the running launch
   double best_split_idem;
   // learned-sequence judge: predicted branch bits and the margin beyond which

@@ -30,6 +30,7 @@ __global__ void init_kernel(State* st, SolveParams p) {
     st->prec = p.prec;
     st->fp64_prefix = p.fp64_prefix;
     st->slice_fmt = p.slice_fmt;
+    st->df64 = p.df64;
     st->tol = p.tol;
     st->emin_override = p.emin_override;
     st->emax_override = p.emax_override;
@@ -112,6 +113,9 @@ __global__ void __launch_bounds__(kEwThreads) x0_kernel(const double* __restrict
   const int64_t n = st->n;
   const int ld = st->ld;
   const double emax = st->emax, width = st->emax - st->emin;
+  const bool df64 = st->df64 != 0;
+  float* Xf = reinterpret_cast<float*>(X);
+  const size_t plane = (size_t)ld * ld;
   double tr = 0.0, fr = 0.0;
   for (int64_t r = blockIdx.x; r < ld; r += gridDim.x) {
     for (int64_t c = threadIdx.x; c < ld; c += kEwThreads) {
@@ -123,7 +127,15 @@ __global__ void __launch_bounds__(kEwThreads) x0_kernel(const double* __restrict
         if (r == c) tr += x;
         fr += x * x;
       }
-      if (write_fp64) X[idx] = x;
+      if (write_fp64) {
+        if (df64) {
+          const float h = (float)x;
+          Xf[idx] = h;
+          Xf[plane + idx] = (float)(x - (double)h);
+        } else {
+          X[idx] = x;
+        }
+      }
       if (write_slices) store_slices<F>(S, idx, x);
     }
   }
@@ -156,6 +168,9 @@ __global__ void __launch_bounds__(kEwThreads) finalize_kernel(const State* __res
   const int k = st->iter & 1;
   const bool from64 = st->x_fp64_valid != 0;
   const double* X = b.x64[k];
+  const float* Xf = reinterpret_cast<const float*>(b.x64[k]);
+  const size_t plane = (size_t)ld * ld;
+  const bool df64 = st->df64 != 0;
   const uint16_t* s0 = b.sl[k][0];
   const uint16_t* s1 = b.sl[k][1];
   const uint16_t* s2 = b.sl[k][2];
@@ -164,7 +179,7 @@ __global__ void __launch_bounds__(kEwThreads) finalize_kernel(const State* __res
       const size_t src = (size_t)r * ld + c;
       double v;
       if (from64) {
-        v = X[src];
+        v = df64 ? (double)Xf[src] + (double)Xf[plane + src] : X[src];
       } else {
         v = join_value_d<F>(s0[src], s1[src], fmt_bf16(F) ? s2[src] : (uint16_t)0);
       }

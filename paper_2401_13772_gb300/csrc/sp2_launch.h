@@ -27,6 +27,7 @@ struct SolveParams {
   int prec;
   int fp64_prefix;
   int slice_fmt;
+  int df64;  // FP64-accurate products in double-float (FP64 buffers hold hi/lo planes)
   double tol;
   double emin_override, emax_override;
 };
@@ -40,6 +41,11 @@ cudaError_t launch_x0(const double* H, const DevBuffers& b, const SolveParams& p
 // One FP64 product step (no-op unless the state says the next product is FP64).
 cudaError_t launch_square_fp64(const DevBuffers& b, int ld, int slice_fmt,
                                unsigned long long cond_handle, cudaStream_t s);
+// One double-float product step on the FP32 pipe (no-op unless the next product
+// is FP64-accurate).
+cudaError_t launch_square_df64(const DevBuffers& b, int ld, int slice_fmt,
+                               unsigned long long cond_handle, cudaStream_t s);
+int df64_tile_count(int ld);
 // One split-precision tcgen05 product step (no-op unless the next product is split).
 cudaError_t launch_square_split(const DevBuffers& b, const SolveParams& p,
                                 unsigned long long cond_handle, cudaStream_t s);

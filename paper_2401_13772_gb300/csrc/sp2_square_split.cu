@@ -281,6 +281,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint16_t* xs2 = buf.sl[src][2];
     uint16_t* out[3] = {buf.sl[dst][0], buf.sl[dst][1], buf.sl[dst][2]};
     double* out64 = buf.x64[dst];
+    // FP64-accurate phases read the next iterate from the FP64 buffer: as
+    // doubles, or as double-float planes (hi = x, lo = 0)
+    const bool df = st->df64 != 0;
+    float* out_hi = reinterpret_cast<float*>(out64);
+    float* out_lo = out_hi + (size_t)ld * ld;
     const bool diag = (I == J);
 #pragma unroll
     for (int ch = 0; ch < BN / 32; ++ch) {
@@ -321,7 +326,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             out[0][m] = a;
             out[1][m] = b2;
             if (fmt_bf16(F)) out[2][m] = c2;
-            if (want_fp64) out64[m] = (double)x;
+            if (want_fp64) {
+              if (df) {
+                out_hi[m] = x;
+                out_lo[m] = 0.0f;
+              } else {
+                out64[m] = (double)x;
+              }
+            }
           }
         }
       }
@@ -333,7 +345,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         pack_store_row<F>(out, d, v0);
         if (want_fp64) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) out64[d + j] = (double)v0[j];
+          for (int j = 0; j < 32; ++j) {
+            if (df) {
+              out_hi[d + j] = v0[j];
+              out_lo[d + j] = 0.0f;
+            } else {
+              out64[d + j] = (double)v0[j];
+            }
+          }
         }
       } else {
 #pragma unroll
@@ -344,7 +363,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             out[0][d + j] = a;
             out[1][d + j] = b2;
             if (fmt_bf16(F)) out[2][d + j] = c2;
-            if (want_fp64) out64[d + j] = (double)v0[j];
+            if (want_fp64) {
+              if (df) {
+                out_hi[d + j] = v0[j];
+                out_lo[d + j] = 0.0f;
+              } else {
+                out64[d + j] = (double)v0[j];
+              }
+            }
           }
         }
       }

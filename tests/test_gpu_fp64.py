@@ -164,3 +164,34 @@ def test_streams_are_independent(pkg):
     assert np.abs(host(D2) - oracle.sp2_plain(H2, n2, 1e-12)["D"]).max() <= TOL_FP64
     pkg.release(s1)
     pkg.release(s2)
+
+
+def test_df64_products_match_plain_sp2(pkg):
+    """Double-float products (pairs of FP32, ~2^-47 relative) track the FP64
+    iterates to ~1e-12 and the whole solve meets the FP64 gate."""
+    H, nocc = cube_hamiltonian(75, 5)  # n = 300, ragged
+    for k in (1, 5):
+        D, info = pkg.sp2_dense_ex(dev(H), nocc, 0.0, prec="df64", maxiter=k,
+                                   raise_on_status=False)
+        ref = oracle.sp2_plain(H, nocc, 0.0, stop_after=k)
+        assert info["bits"] == ref["bits"]
+        assert np.abs(host(D) - ref["D"]).max() <= 1e-11
+    for sites, seed in ((75, 2), (250, 4)):
+        H, nocc = cube_hamiltonian(sites, seed)
+        w, V = oracle.jacobi_eigh(H)
+        Dref, _ = oracle.density_projector(w, V, nocc)
+        D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-10, prec="df64")
+        assert info["status"] == "OK" and info["converged"]
+        assert np.abs(host(D) - Dref).max() <= TOL_FP64
+
+
+def test_mixed_with_native_and_double_float_fp64_phases(pkg):
+    H, nocc = cube_hamiltonian(250, 4)
+    w, V = oracle.jacobi_eigh(H)
+    Dref, _ = oracle.density_projector(w, V, nocc)
+    for impl in (0, 1):
+        D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-10, prec="mixed_fp16", fp64_impl=impl)
+        assert info["status"] == "OK" and info["converged"]
+        Dn = host(D)
+        assert np.abs(Dn - Dref).max() <= 1e-5
+        assert abs(np.trace(Dn) - nocc) <= 1e-8
