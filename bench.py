@@ -41,6 +41,7 @@ NOMINAL_BF16_TFLOPS = 2250.0
 # stands, keyed by (kernel, n); see profiles/.
 NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200}
 NOMINAL_FP64_TFLOPS = 1.25
+DF_OPS = 15  # FP32 instructions per double-float multiply-add in square_df64_kernel
 
 
 def parse_args():
@@ -50,7 +51,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed_fp16",
-                    choices=["fp64", "fp32_split", "mixed_fp16", "mixed_bf16"])
+                    choices=["fp64", "df64", "fp32_split", "fp32_split_bf16", "mixed_fp16",
+                             "mixed_bf16"])
+    ap.add_argument("--fp64-impl", type=int, default=0,
+                    help="mixed modes: 0 = double-float FP64-accurate products, 1 = native FP64")
     ap.add_argument("--sites", type=int, default=1024)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -466,13 +470,14 @@ def main():
             e.record()
         return evs
 
-    opts = dict(prec=args.prec, fp64_prefix=args.fp64_prefix, loop_mode=args.loop_mode)
+    opts = dict(prec=args.prec, fp64_prefix=args.fp64_prefix, loop_mode=args.loop_mode,
+                fp64_impl=args.fp64_impl)
     # warm-up (builds the loop graph) and the iteration count
     info = None
     for _ in range(max(1, args.warmup)):
         _, info = pkg.sp2_dense_ex(H, nocc, args.tol, D=D, **opts)
     iters = info["iters"]
-    body_kernels = 1 if args.prec in ("fp64", "fp32_split") else 2
+    body_kernels = 1 if args.prec in ("fp64", "df64", "fp32_split", "fp32_split_bf16") else 2
     if args.loop_mode == 0:
         launches_per_solve = 3 + body_kernels * max(iters, 1) + 1
     else:
@@ -540,15 +545,24 @@ def main():
     n_fp64 = phases[0] + phases[2]
     n_split = phases[1]
 
-    def roof(kernel, ms, peak, note):
+    def roof(kernel, ms, peak, note, bound="tensor"):
         ach = flops_alg / (ms * 1e-3) / 1e12
-        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+        return {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": NCU_TRAFFIC.get((kernel, n)), "kernel": kernel,
                 "peak_source": note,
                 "flops_per_launch": flops_alg, "avg_launch_ms": ms}
 
     note64 = f"fp64: {peak_src} bf16 burst x nominal fp64/bf16 ratio (1.25/2250)"
     note16 = f"fp16/bf16 dense, {peak_src} burst"
+    # double-float products: FP32 pipe, 152 SMs x 128 lanes x max SM clock,
+    # DF_OPS FP32 instructions per double-float multiply-add (2 flops)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    df_peak = 152 * 128 * sm_mhz * 1e6 * 2.0 / DF_OPS / 1e12
+    notedf = (f"double-float: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz x 2 flops / "
+              f"{DF_OPS} FP32 instructions per multiply-add")
+    df = args.prec == "df64" or (args.prec.startswith("mixed") and args.fp64_impl == 0)
+    k64 = "square_df64_kernel (double-float, FP32 pipe)" if df else "square_fp64_kernel (FP64 DMMA)"
+    p64, n64, b64 = (df_peak, notedf, "alu") if df else (fp64_peak, note64, "tensor")
     split_ms = None
     if n_split > 0:
         if n_fp64 == 0:
@@ -565,25 +579,32 @@ def main():
     if n_fp64 > 0:
         fp64_ms = (loop_mean - n_split * (split_ms or 0.0)) / n_fp64
     if fp64_ms is not None and (split_ms is None or n_fp64 * fp64_ms >= n_split * split_ms):
-        roofline = roof("square_fp64_kernel (FP64 DMMA)", fp64_ms, fp64_peak, note64)
+        roofline = roof(k64, fp64_ms, p64, n64, b64)
         secondary = roof("square_split_kernel (tcgen05)", split_ms, bf16_peak, note16) \
             if split_ms else None
     else:
         roofline = roof("square_split_kernel (tcgen05)", split_ms, bf16_peak, note16)
-        secondary = roof("square_fp64_kernel (FP64 DMMA)", fp64_ms, fp64_peak, note64) \
-            if fp64_ms else None
+        secondary = roof(k64, fp64_ms, p64, n64, b64) if fp64_ms else None
     if secondary is not None:
         roofline["secondary"] = secondary
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32_split": "f16x2 split, f32 accumulate, f64 traces",
-                      "mixed_fp16": "f64 prefix/refine + f16x2 split",
-                      "mixed_bf16": "f64 prefix/refine + bf16x3 split"}[args.prec],
+            "dtype": {"fp64": "f64", "df64": "double-float (f32 pairs)",
+                      "fp32_split": "f16x2 split, f32 accumulate, f64 traces",
+                      "fp32_split_bf16": "bf16x3 split, f32 accumulate, f64 traces",
+                      "mixed_fp16": ("double-float" if args.fp64_impl == 0 else "f64") +
+                      " prefix/refine + f16x2 split",
+                      "mixed_bf16": ("double-float" if args.fp64_impl == 0 else "f64") +
+                      " prefix/refine + bf16x3 split"}[args.prec],
             "data": "synthetic",
             "config": {"workload": workload_name(args.sites, args.seed), "n": n, "nocc": nocc,
                        "prec": args.prec, "tol": args.tol, "rule": "nearer",
+                       "fp64_prefix": args.fp64_prefix,
+                       "fp64_accurate_products": ("double-float" if args.prec == "df64" or
+                                                  (args.prec.startswith("mixed") and
+                                                   args.fp64_impl == 0) else "native fp64"),
                        "parallelism": f"replicas x{world}",
                        "l2": "flushed before each step (256 MiB write, outside events)"},
             "iters": iters, "status": qinfo["status"], "phase_iters": qinfo["phase_iters"],
@@ -642,7 +663,7 @@ def main():
         sec = time.perf_counter() - t0
         err = float(np.abs(D_main.cpu().numpy() - ref["D"]).max())
         line["d_check"]["max_abs_err_vs_oracle"] = err
-        line["d_check"]["gate"] = 1e-10 if args.prec == "fp64" else 1e-5
+        line["d_check"]["gate"] = 1e-10 if args.prec in ("fp64", "df64") else 1e-5
         line["d_check"]["oracle_iters"] = ref["iters"]
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": cpu_cores(),
                                 "kind": "oracle",
