@@ -41,7 +41,7 @@ NOMINAL_BF16_TFLOPS = 2250.0
 # stands, keyed by (kernel, n); see profiles/.
 NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200}
 NOMINAL_FP64_TFLOPS = 1.25
-DF_OPS = 15  # FP32 instructions per double-float multiply-add in square_df64_kernel
+DF_OPS = 12  # FP32 instructions per double-float multiply-add in square_df64_kernel
 
 
 def parse_args():

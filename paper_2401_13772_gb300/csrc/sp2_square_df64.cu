@@ -5,11 +5,13 @@
 // about 48 significant bits; Dekker 1971, "A floating-point technique for
 // extending the available precision"). The product of two pairs uses the
 // exact product error of an FMA (p = a_hi b_hi, e = fma(a_hi, b_hi, -p)) and
-// the sum uses Knuth's two-sum, so a multiply-add costs about eleven FP32
-// instructions. On this part the FP32 pipe issues about six times more of
-// those per second than the FP64 pipe issues DFMAs, which makes double-float
-// the faster way to FP64-class products (relative error ~2^-47 per product,
-// far below what the SP2 prefix and refinement phases need).
+// the sum uses Knuth's two-sum; the dot product is compensated (the errors
+// of all terms collect in a second float, renormalized once at the end), so a
+// multiply-add costs twelve FP32 instructions. On this part the FP32 pipe
+// issues several times more of those per second than the FP64 pipe issues
+// DFMAs, which makes double-float the faster way to FP64-class products
+// (relative error ~2^-45 per product, far below what the SP2 prefix and
+// refinement phases need).
 //
 // Layout: an iterate in double-float form occupies the FP64 ping-pong buffer
 // of the workspace as two float planes, hi then lo, each ld x ld row-major.
@@ -51,7 +53,8 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-// c += a * b in double-float
+// c += a * b in double-float, renormalized every step (used where few terms
+// are summed)
 __device__ __forceinline__ void df_fma(float& ch, float& cl, float ah, float al, float bh,
                                        float bl) {
   const float p = ah * bh;
@@ -66,6 +69,23 @@ __device__ __forceinline__ void df_fma(float& ch, float& cl, float ah, float al,
   // renormalize
   ch = s + lo;
   cl = lo - (ch - s);
+}
+
+// One term of a compensated dot product (Ogita, Rump & Oishi 2005, "Dot2"):
+// the exact product error (FMA) and the exact addition error (two-sum) go to
+// a separate float c; s + c is renormalized once, after the last term.
+// Twelve FP32 instructions per multiply-add of double-float operands.
+__device__ __forceinline__ void dot2_step(float& s, float& c, float ah, float al, float bh,
+                                          float bl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float s1 = s + p;
+  const float v = s1 - s;
+  const float q = (s - (s1 - v)) + (p - v);
+  c += q + e;
+  s = s1;
 }
 
 // (ah, al) * k for an exact power-of-two k is exact; 2a - s in double-float:
@@ -163,7 +183,7 @@ __global__ void __launch_bounds__(THREADS, 1) square_df64_kernel(DevBuffers buf,
     const float(*Al)[BT] = sm.Al[s];
     const float(*Bh)[BT] = same ? sm.Ah[s] : sm.Bh[s];
     const float(*Bl)[BT] = same ? sm.Al[s] : sm.Bl[s];
-#pragma unroll 2
+#pragma unroll 1
     for (int k = 0; k < BKD; ++k) {
       float ah[8], al[8], bh[8], bl[8];
       *reinterpret_cast<float4*>(&ah[0]) = *reinterpret_cast<const float4*>(&Ah[k][ty * 4]);
@@ -177,7 +197,7 @@ __global__ void __launch_bounds__(THREADS, 1) square_df64_kernel(DevBuffers buf,
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) df_fma(ch[i][j], cl[i][j], ah[i], al[i], bh[j], bl[j]);
+        for (int j = 0; j < 8; ++j) dot2_step(ch[i][j], cl[i][j], ah[i], al[i], bh[j], bl[j]);
     }
     __syncthreads();
   }
@@ -193,7 +213,9 @@ __global__ void __launch_bounds__(THREADS, 1) square_df64_kernel(DevBuffers buf,
     for (int j = 0; j < 8; ++j) {
       const int c = row_b + tx * 4 + (j & 3) + (j >> 2) * 64;
       if (r > c) continue;  // covered by the mirror of the tile above the diagonal
-      float xh = ch[i][j], xl = cl[i][j];
+      // renormalize the compensated sum into a double-float pair
+      float xh = ch[i][j] + cl[i][j];
+      float xl = cl[i][j] - (xh - ch[i][j]);
       if (bit) {
         const size_t g = (size_t)r * ld + c;
         df_sub(2.0f * Xh[g], 2.0f * Xl[g], xh, xl, xh, xl);
