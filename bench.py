@@ -58,7 +58,7 @@ def parse_args():
     ap.add_argument("--sites", type=int, default=1024)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--fp64-prefix", type=int, default=10)
+    ap.add_argument("--fp64-prefix", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
