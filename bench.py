@@ -39,7 +39,8 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 NOMINAL_BF16_TFLOPS = 2250.0
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands, keyed by (kernel, n); see profiles/.
-NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200}
+NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200,
+               ("square_df64_kernel (double-float, FP32 pipe)", 4096): 521512448}
 NOMINAL_FP64_TFLOPS = 1.25
 DF_OPS = 12  # FP32 instructions per double-float multiply-add in square_df64_kernel
 

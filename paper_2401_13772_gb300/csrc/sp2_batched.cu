@@ -59,7 +59,14 @@ struct BCfg {
   static constexpr int NS = fmt_slices(F);
   static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
   static constexpr int STAGES = fmt_bf16(F) ? 2 : 3;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  // epilogue staging (per epilogue warp): a 32 x 33 word plane holding the
+  // packed (slice0, slice1) of a 32 x 32 chunk, and for BF16x3 a 32 x 34
+  // half-word plane for slice 2; used to turn row-wise results into
+  // column-contiguous (coalesced) stores
+  static constexpr int EPI_A = 32 * 33;
+  static constexpr int EPI_B = 32 * 34;
+  static constexpr int EPI_BYTES = 4 * (EPI_A * 4 + (NS == 3 ? EPI_B * 2 : 0));
+  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
 };
 
 struct Maps {
@@ -97,6 +104,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   const bool epi = warp >= EPI_WARP0;
   const int erow = threadIdx.x - EPI_WARP0 * 32;  // tile row of an epilogue thread
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  unsigned char* const epi_base = smem_raw + (base - smem_u32(smem_raw)) + STAGES * STAGE_BYTES;
+  uint32_t* const epA = reinterpret_cast<uint32_t*>(epi_base) +
+                        (epi ? (warp - EPI_WARP0) * BCfg<F>::EPI_A : 0);
+  uint16_t* const epB = reinterpret_cast<uint16_t*>(epi_base + 4 * BCfg<F>::EPI_A * 4) +
+                        (epi ? (warp - EPI_WARP0) * BCfg<F>::EPI_B : 0);
   const uint32_t bars = smem_u32(&sh.bars[0]);
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 8u * (STAGES + s); };
@@ -352,10 +364,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (r <= c) {
                   uint16_t a, b, c2;
                   split_value_f<F>(x, a, b, c2);
-                  const size_t dd = (size_t)(in.row0 + r) * P + c;
-                  o0[dd] = a;
-                  o1[dd] = b;
-                  if (NS == 3) o2[dd] = c2;
+                  // (r, c) goes through the staging planes; its mirror
+                  // (c, r) is already contiguous across the warp's lanes
+                  epA[lane * 33 + j] = (uint32_t)a | ((uint32_t)b << 16);
+                  if (NS == 3) epB[lane * 34 + j] = c2;
                   if (r == c) {
                     trf += x;
                     frf += x * x;
@@ -370,6 +382,21 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
               tr += (double)trf;
               fr += (double)frf;
+              // rows of the chunk, one per store instruction, lanes along c
+              __syncwarp();
+              const int rb = I * BM + (warp - EPI_WARP0) * 32;
+              const int cc = c0 + lane;
+#pragma unroll 4
+              for (int i = 0; i < 32; ++i) {
+                if (rb + i <= cc) {
+                  const uint32_t v = epA[i * 33 + lane];
+                  const size_t dd = (size_t)(in.row0 + rb + i) * P + cc;
+                  o0[dd] = (uint16_t)(v & 0xffffu);
+                  o1[dd] = (uint16_t)(v >> 16);
+                  if (NS == 3) o2[dd] = epB[i * 34 + lane];
+                }
+              }
+              __syncwarp();
             }
           }
           tc_fence_before();
