@@ -43,6 +43,20 @@ NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200,
                ("square_df64_kernel (double-float, FP32 pipe)", 4096): 521512448}
 NOMINAL_FP64_TFLOPS = 1.25
 DF_OPS = 12  # FP32 instructions per double-float multiply-add in square_df64_kernel
+OZ_PRODUCTS = 15  # BF16 digit products per FP64-accurate product in square_oz_kernel
+IMPL_DTYPE = {"double-float": "double-float", "native fp64": "f64",
+              "digits": "bf16 digit products (f32 accumulate)"}
+
+
+def fp64_impl_kind(args):
+    """Arithmetic of the FP64-accurate products of the run."""
+    if args.prec == "df64":
+        return "double-float"
+    if args.prec.startswith("mixed"):
+        if args.fp64_impl == 0:  # the library default
+            return "digits" if 4 * args.sites <= 8192 else "double-float"
+        return {1: "native fp64", 2: "double-float", 3: "digits"}[args.fp64_impl]
+    return "native fp64"
 
 
 def parse_args():
@@ -54,8 +68,9 @@ def parse_args():
     ap.add_argument("--prec", default="mixed_fp16",
                     choices=["fp64", "df64", "fp32_split", "fp32_split_bf16", "mixed_fp16",
                              "mixed_bf16"])
-    ap.add_argument("--fp64-impl", type=int, default=0,
-                    help="mixed modes: 0 = double-float FP64-accurate products, 1 = native FP64")
+    ap.add_argument("--fp64-impl", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="mixed modes, FP64-accurate products: 0 = library default, 1 = native "
+                         "FP64, 2 = double-float, 3 = tensor-core digit products")
     ap.add_argument("--sites", type=int, default=1024)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -74,6 +89,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=4000)
     ap.add_argument("--batch-prec", default="fp32_split",
                     choices=["fp32_split", "fp32_split_bf16"])
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="batched workload: skip the launch-configuration autotuner")
     ap.add_argument("--train-count", type=int, default=20000)
     ap.add_argument("--eval-count", type=int, default=1000)
     ap.add_argument("--eval-sites", type=int, default=512)
@@ -235,6 +252,14 @@ def run_batched(args):
     H = Hh.to(dev)
     D = torch.empty_like(H)
     stream = torch.cuda.current_stream()
+    tune = None
+    if args.tune:
+        # the launch-configuration autotuner, on every k-th part in size order
+        # (outside the timed region); later launches use its choice
+        stride = max(1, args.batch // 600)
+        tune = pkg.batched_tune(H, n, offsets, nocc, 1e-10, D_packed=D, prec=args.batch_prec,
+                                sample_stride=stride, reps=3)
+        tune["sample_stride"] = stride
     for _ in range(max(1, args.warmup)):
         D, iters, status = pkg.sp2_batched(H, n, offsets, nocc, 1e-10, D_packed=D,
                                            prec=args.batch_prec)
@@ -252,6 +277,15 @@ def run_batched(args):
     sec = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(K)) / K / 1e3
     it = iters.cpu().numpy()
     st = status.cpu().numpy()
+    # per-part SM cycles of one more launch, by row blocks of 128 (outside the timing)
+    _, _, _, cyc = pkg.sp2_batched(H, n, offsets, nocc, 1e-10, D_packed=D,
+                                   prec=args.batch_prec, cycles=True)
+    cyc = cyc.cpu().numpy().astype(np.float64)
+    blocks = (n + 127) // 128
+    by_blocks = {int(b): {"parts": int((blocks == b).sum()),
+                          "mean_mcycles": round(float(cyc[blocks == b].mean()) / 1e6, 3),
+                          "share_of_cycles": round(float(cyc[blocks == b].sum() / cyc.sum()), 3)}
+                 for b in np.unique(blocks)}
     nn = n.astype(np.float64)
     flops = float(np.sum(it * nn * nn * (nn + 1)))
     peaks, src = load_peaks()
@@ -324,7 +358,9 @@ def run_batched(args):
             "e2e": {"value": args.batch / e2e_sec, "unit": UNIT,
                     "h2d_bytes_per_step": int(packed.nbytes),
                     "d2h_bytes_per_step": int(packed.nbytes)},
-            "gpu_launches": K, "clocks": clk}
+            "gpu_launches": K, "clocks": clk,
+            "launch_config": tune if tune is not None else "library default",
+            "cycles_by_row_blocks": by_blocks}
     print(json.dumps(line), flush=True)
 
 
@@ -478,7 +514,9 @@ def main():
     for _ in range(max(1, args.warmup)):
         _, info = pkg.sp2_dense_ex(H, nocc, args.tol, D=D, **opts)
     iters = info["iters"]
-    body_kernels = 1 if args.prec in ("fp64", "df64", "fp32_split", "fp32_split_bf16") else 2
+    impl = fp64_impl_kind(args)
+    body_kernels = 1 if args.prec in ("fp64", "df64", "fp32_split", "fp32_split_bf16") else \
+        (3 if impl == "digits" else 2)
     if args.loop_mode == 0:
         launches_per_solve = 3 + body_kernels * max(iters, 1) + 1
     else:
@@ -561,9 +599,16 @@ def main():
     df_peak = 152 * 128 * sm_mhz * 1e6 * 2.0 / DF_OPS / 1e12
     notedf = (f"double-float: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz x 2 flops / "
               f"{DF_OPS} FP32 instructions per multiply-add")
-    df = args.prec == "df64" or (args.prec.startswith("mixed") and args.fp64_impl == 0)
-    k64 = "square_df64_kernel (double-float, FP32 pipe)" if df else "square_fp64_kernel (FP64 DMMA)"
-    p64, n64, b64 = (df_peak, notedf, "alu") if df else (fp64_peak, note64, "tensor")
+    if impl == "double-float":
+        k64, p64, n64, b64 = ("square_df64_kernel (double-float, FP32 pipe)", df_peak, notedf,
+                              "alu")
+    elif impl == "digits":
+        k64, p64, b64 = ("square_oz_kernel + digits_kernel (BF16 digit products, tcgen05)",
+                         bf16_peak / OZ_PRODUCTS, "tensor")
+        n64 = (f"fp16/bf16 dense, {peak_src} burst / {OZ_PRODUCTS} BF16 digit products per "
+               f"FP64-accurate product")
+    else:
+        k64, p64, n64, b64 = ("square_fp64_kernel (FP64 DMMA)", fp64_peak, note64, "tensor")
     split_ms = None
     if n_split > 0:
         if n_fp64 == 0:
@@ -595,17 +640,14 @@ def main():
             "dtype": {"fp64": "f64", "df64": "double-float (f32 pairs)",
                       "fp32_split": "f16x2 split, f32 accumulate, f64 traces",
                       "fp32_split_bf16": "bf16x3 split, f32 accumulate, f64 traces",
-                      "mixed_fp16": ("double-float" if args.fp64_impl == 0 else "f64") +
-                      " prefix/refine + f16x2 split",
-                      "mixed_bf16": ("double-float" if args.fp64_impl == 0 else "f64") +
-                      " prefix/refine + bf16x3 split"}[args.prec],
+                      "mixed_fp16": IMPL_DTYPE[impl] + " prefix/refine + f16x2 split",
+                      "mixed_bf16": IMPL_DTYPE[impl] + " prefix/refine + bf16x3 split"}[
+                          args.prec],
             "data": "synthetic",
             "config": {"workload": workload_name(args.sites, args.seed), "n": n, "nocc": nocc,
                        "prec": args.prec, "tol": args.tol, "rule": "nearer",
                        "fp64_prefix": args.fp64_prefix,
-                       "fp64_accurate_products": ("double-float" if args.prec == "df64" or
-                                                  (args.prec.startswith("mixed") and
-                                                   args.fp64_impl == 0) else "native fp64"),
+                       "fp64_accurate_products": impl,
                        "parallelism": f"replicas x{world}",
                        "l2": "flushed before each step (256 MiB write, outside events)"},
             "iters": iters, "status": qinfo["status"], "phase_iters": qinfo["phase_iters"],

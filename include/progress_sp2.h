@@ -88,8 +88,11 @@ typedef struct {
                            right before and right after the product loop, so a
                            caller can time the products alone */
   int32_t fp64_impl;    /* MIXED_*: arithmetic of the FP64-accurate products (prefix and
-                           refinement): 0 = double-float on the FP32 pipe (default),
-                           1 = native FP64 (DMMA) */
+                           refinement): 0 = library default (3 for n <= 8192, else 2),
+                           1 = native FP64 (DMMA), 2 = double-float on the FP32 pipe,
+                           3 = exact products of BF16 fixed-point digits on the tensor
+                           cores (Ozaki scheme; ~2^-40 absolute accuracy; n <= 8192, else
+                           PROGRESS_EUNSUPPORTED) */
   int32_t reserved[3];  /* must be zero */
 } progress_opts_t;
 
@@ -97,7 +100,9 @@ typedef struct {
 typedef struct {
   int32_t status;        /* progress_status_t of the solve */
   int32_t iters;         /* products performed */
-  int32_t converged;     /* 1 if |Tr X^2 - Tr X| < tol was reached */
+  int32_t converged;     /* 1 if |Tr X^2 - Tr X| < tol was reached, or (MIXED modes) the
+                            refinement stopped on the round-off floor of its products
+                            (two steps without halving the error) */
   int32_t phase_iters[3];/* products in FP64 prefix / split phase / FP64 refinement */
   double emin, emax;     /* bounds used */
   double trace;          /* Tr D */
@@ -168,7 +173,7 @@ progress_status_t progress_sp2_dense_noalloc(const double* dH, int64_t n, int64_
 
 /*
  * Batched SP2: `batch` independent dense problems of uneven size -- the parts
- * of a graph-partitioned system, solved "independently and concurrently"
+ * of a graph-partitioned system, which are independent and solved concurrently
  * (§VIII.B) -- in one persistent kernel launch (captured once in a CUDA graph
  * and replayed while the batch layout and pointers stay the same). Each CTA
  * takes whole instances, largest first, from a device work queue and runs
@@ -206,7 +211,15 @@ typedef struct {
   int32_t* d_products;         /* device [batch]: products executed in total, including a
                                   rejected predicted run (d_iters counts the final run only),
                                   or NULL */
-  int32_t reserved[6];         /* must be zero */
+  int32_t tile_n;              /* launch configuration (0 = the tuned or default one): product
+                                  tile width, 64 or 128 (tiles are 128 x tile_n) */
+  int32_t cluster;             /* CTAs per thread-block cluster: 1, 2, 4 or 8 */
+  int32_t share;               /* an instance of at least `share` 128-row blocks is solved by
+                                  a whole cluster (tiles dealt to its CTAs), a smaller one by
+                                  one CTA; >= 1 */
+  int32_t reserved0;           /* must be zero */
+  int64_t* d_cycles;           /* device [batch]: SM clock cycles spent on each instance (by
+                                  the CTA that owns it, or cluster rank 0), or NULL */
 } progress_batch_ex_t;
 
 /*
@@ -223,6 +236,39 @@ progress_status_t progress_sp2_batched_ex(int32_t batch, const int32_t* h_n,
                                           int32_t* d_iters, int32_t* d_status,
                                           const progress_opts_t* opts,
                                           const progress_batch_ex_t* ex, void* stream);
+
+/*
+ * Autotuner of the batched solver's launch configuration. No part of the
+ * paper corresponds to it: it picks the tile shape (128 x 64 or 128 x 128
+ * product tiles), the cluster size (1, 2, 4 or 8 CTAs) and the sharing
+ * threshold of progress_sp2_batched for a batch by timing candidate
+ * configurations on the GPU.
+ *   Arguments as progress_sp2_batched (H and D as there; D is overwritten for
+ *   the instances of the sample). sample_stride >= 1: the calibration runs on
+ *   every sample_stride-th instance in size order (1 = the whole batch).
+ *   The best configuration is cached in the library under the batch's size
+ *   signature (device, slice format, largest padded order, log2 of the batch
+ *   size); later progress_sp2_batched(_ex) calls with the same signature and
+ *   no explicit configuration use it.
+ *   out (host, may be NULL): the chosen configuration and each candidate's
+ *   time per launch (milliseconds, median of `reps` timed launches after one
+ *   untimed one).
+ * Synchronizes the stream (it measures with CUDA events). Errors as
+ * progress_sp2_batched.
+ */
+typedef struct {
+  int32_t tile_n, cluster, share; /* chosen configuration */
+  int32_t ncand;                   /* candidates timed (<= 16) */
+  int32_t cand[16][3];             /* tile_n, cluster, share of each candidate */
+  float ms[16];                    /* time per launch of each candidate */
+} progress_batch_tune_t;
+
+progress_status_t progress_sp2_batched_tune(int32_t batch, const int32_t* h_n,
+                                            const int64_t* h_offset, const int32_t* h_nocc,
+                                            const double* dH, double tol, double* dD,
+                                            const progress_opts_t* opts, int32_t sample_stride,
+                                            int32_t reps, progress_batch_tune_t* out,
+                                            void* stream);
 
 /*
  * Features of the learned predictor, 37 floats per instance (device output

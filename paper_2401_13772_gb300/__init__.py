@@ -135,34 +135,80 @@ def pack_batch(mats):
     return packed, n, offsets
 
 
-def sp2_batched(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", maxiter=100,
-                stream=None, prec="fp32_split"):
-    """Batched split-precision SP2 over packed device inputs.
-
-    H_packed: 1-D float64 CUDA tensor; n, offsets, nocc: host int sequences.
-    Returns (D_packed, iters, status) with iters/status as int32 CUDA tensors.
-    """
+def _batch_arrays(n, offsets, nocc):
     import numpy as np
+    return (np.ascontiguousarray(n, dtype=np.int32), np.ascontiguousarray(offsets, dtype=np.int64),
+            np.ascontiguousarray(nocc, dtype=np.int32))
+
+
+def _check_packed(H_packed):
     import torch
     if not (isinstance(H_packed, torch.Tensor) and H_packed.is_cuda and
             H_packed.dtype == torch.float64 and H_packed.dim() == 1 and H_packed.is_contiguous()):
         raise TypeError("H_packed must be a contiguous 1-D float64 CUDA tensor")
-    n = np.ascontiguousarray(n, dtype=np.int32)
-    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
-    nocc = np.ascontiguousarray(nocc, dtype=np.int32)
+
+
+def sp2_batched(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", maxiter=100,
+                stream=None, prec="fp32_split", config=None, cycles=False):
+    """Batched split-precision SP2 over packed device inputs.
+
+    H_packed: 1-D float64 CUDA tensor; n, offsets, nocc: host int sequences.
+    config: None (the autotuned configuration for this batch signature, else
+    the library default) or (tile_n, cluster, share).
+    Returns (D_packed, iters, status) with iters/status as int32 CUDA tensors,
+    plus a per-instance int64 tensor of SM clock cycles when cycles=True.
+    """
+    import torch
+    _check_packed(H_packed)
+    n, offsets, nocc = _batch_arrays(n, offsets, nocc)
     b = len(n)
     if D_packed is None:
         D_packed = torch.empty_like(H_packed)
     iters = torch.zeros(b, dtype=torch.int32, device=H_packed.device)
     status = torch.zeros(b, dtype=torch.int32, device=H_packed.device)
     o = make_opts(prec=prec, rule=rule, maxiter=maxiter)
+    cyc = None
     with torch.cuda.device(H_packed.device):
-        check(load().progress_sp2_batched(
-            b, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(offsets.ctypes.data),
-            ctypes.c_void_p(nocc.ctypes.data), ctypes.c_void_p(H_packed.data_ptr()), float(tol),
-            ctypes.c_void_p(D_packed.data_ptr()), ctypes.c_void_p(iters.data_ptr()),
-            ctypes.c_void_p(status.data_ptr()), ctypes.byref(o), _stream_ptr(stream)))
+        args = (b, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(offsets.ctypes.data),
+                ctypes.c_void_p(nocc.ctypes.data), ctypes.c_void_p(H_packed.data_ptr()),
+                float(tol), ctypes.c_void_p(D_packed.data_ptr()),
+                ctypes.c_void_p(iters.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                ctypes.byref(o))
+        if config is None and not cycles:
+            check(load().progress_sp2_batched(*args, _stream_ptr(stream)))
+        else:
+            ex = _lib.BatchEx()
+            if config is not None:
+                ex.tile_n, ex.cluster, ex.share = (int(v) for v in config)
+            if cycles:
+                cyc = torch.zeros(b, dtype=torch.int64, device=H_packed.device)
+                ex.d_cycles = cyc.data_ptr()
+            check(load().progress_sp2_batched_ex(*args, ctypes.byref(ex), _stream_ptr(stream)))
+    if cycles:
+        return D_packed, iters, status, cyc
     return D_packed, iters, status
+
+
+def batched_tune(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", maxiter=100,
+                 stream=None, prec="fp32_split", sample_stride=1, reps=3):
+    """Run the batched launch-configuration autotuner on this batch (writes D
+    for the sampled instances) and return its report: the chosen tile_n,
+    cluster, share and each candidate's time per launch. Later sp2_batched
+    calls with the same batch signature use the chosen configuration."""
+    import torch
+    _check_packed(H_packed)
+    n, offsets, nocc = _batch_arrays(n, offsets, nocc)
+    if D_packed is None:
+        D_packed = torch.empty_like(H_packed)
+    o = make_opts(prec=prec, rule=rule, maxiter=maxiter)
+    out = _lib.BatchTune()
+    with torch.cuda.device(H_packed.device):
+        check(load().progress_sp2_batched_tune(
+            len(n), ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(offsets.ctypes.data),
+            ctypes.c_void_p(nocc.ctypes.data), ctypes.c_void_p(H_packed.data_ptr()), float(tol),
+            ctypes.c_void_p(D_packed.data_ptr()), ctypes.byref(o), int(sample_stride), int(reps),
+            ctypes.byref(out), _stream_ptr(stream)))
+    return out.to_dict()
 
 
 def history(stream=None, cap=256):

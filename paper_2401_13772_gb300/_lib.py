@@ -51,7 +51,21 @@ class BatchEx(ctypes.Structure):
                 ("d_pred_len", ctypes.c_void_p), ("judge_delta", ctypes.c_double),
                 ("d_bits_out", ctypes.c_void_p), ("d_bounds_out", ctypes.c_void_p),
                 ("d_fallback", ctypes.c_void_p), ("d_products", ctypes.c_void_p),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("tile_n", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("share", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("d_cycles", ctypes.c_void_p)]
+
+
+class BatchTune(ctypes.Structure):
+    _fields_ = [("tile_n", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("share", ctypes.c_int32), ("ncand", ctypes.c_int32),
+                ("cand", (ctypes.c_int32 * 3) * 16), ("ms", ctypes.c_float * 16)]
+
+    def to_dict(self):
+        return {"tile_n": self.tile_n, "cluster": self.cluster, "share": self.share,
+                "candidates": [{"tile_n": self.cand[i][0], "cluster": self.cand[i][1],
+                                "share": self.cand[i][2], "ms": round(float(self.ms[i]), 3)}
+                               for i in range(self.ncand)]}
 
 
 # symbol -> (restype, argtypes); every function declared in include/progress_sp2.h
@@ -69,6 +83,9 @@ SIGNATURES = {
                                             ctypes.POINTER(Opts), _P]),
     "progress_sp2_batched_ex": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _D, _P, _P, _P,
                                                ctypes.POINTER(Opts), ctypes.POINTER(BatchEx), _P]),
+    "progress_sp2_batched_tune": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _D, _P,
+                                                 ctypes.POINTER(Opts), ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.POINTER(BatchTune), _P]),
     "progress_features": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P]),
     "progress_trace_hd": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
     "progress_mlp_param_count": (ctypes.c_int32, [ctypes.c_int32] * 3),

@@ -44,13 +44,14 @@ struct Workspace {
   int ld_cap = 0;       // ld the matrix buffers were sized for
   int x64_cap = 0;      // ld of the FP64 ping-pong buffers (0 = none)
   int slices_cap = 0;   // slices per set that are allocated
+  int digits_cap = 0;   // ld of the digit planes (0 = none)
   sp2::DevBuffers buf{};
   sp2::State* h_state = nullptr;  // pinned host mirror for readback
   cudaStream_t cap_stream = nullptr;
   // cached loop graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int g_ld = -1, g_prec = -1, g_fmt = -1, g_df = -1;
+  int g_ld = -1, g_prec = -1, g_fmt = -1, g_df = -1, g_oz = -1;
 };
 
 std::mutex g_mu;
@@ -61,7 +62,7 @@ void free_graph(Workspace* w) {
   if (w->graph) cudaGraphDestroy(w->graph);
   w->exec = nullptr;
   w->graph = nullptr;
-  w->g_ld = w->g_prec = w->g_fmt = w->g_df = -1;
+  w->g_ld = w->g_prec = w->g_fmt = w->g_df = w->g_oz = -1;
 }
 
 void free_matrices(Workspace* w) {
@@ -73,10 +74,14 @@ void free_matrices(Workspace* w) {
       w->buf.sl[k][i] = nullptr;
     }
   }
+  for (int d = 0; d < 5; ++d) {
+    if (w->buf.dg[d]) cudaFree(w->buf.dg[d]);
+    w->buf.dg[d] = nullptr;
+  }
   if (w->buf.partials) cudaFree(w->buf.partials);
   w->buf.partials = nullptr;
   w->buf.max_partials = 0;
-  w->x64_cap = w->slices_cap = w->ld_cap = 0;
+  w->x64_cap = w->slices_cap = w->ld_cap = w->digits_cap = 0;
 }
 
 void free_workspace(Workspace* w) {
@@ -115,18 +120,22 @@ progress_status_t get_workspace(cudaStream_t s, Workspace** out) {
 }
 
 // Make sure the matrix buffers cover ld and the requested formats.
-progress_status_t ensure_buffers(Workspace* w, int ld, bool need_x64, int nslices) {
+progress_status_t ensure_buffers(Workspace* w, int ld, bool need_x64, int nslices,
+                                 bool need_digits = false) {
   const bool grow = ld > w->ld_cap || (need_x64 && w->x64_cap < ld) ||
-                    (nslices > 0 && (w->slices_cap < nslices || w->ld_cap < ld));
+                    (nslices > 0 && (w->slices_cap < nslices || w->ld_cap < ld)) ||
+                    (need_digits && w->digits_cap < ld);
   if (!grow && w->buf.partials) return PROGRESS_OK;
   CK(cudaStreamSynchronize(w->stream), "cudaStreamSynchronize");
   const int new_ld = ld > w->ld_cap ? ld : w->ld_cap;
   const bool keep_x64 = w->x64_cap > 0;
+  const bool keep_dg = w->digits_cap > 0;
   const int keep_sl = w->slices_cap;
   free_graph(w);
   free_matrices(w);
   const size_t elems = (size_t)new_ld * new_ld;
   const bool x64 = need_x64 || keep_x64;
+  const bool dg = need_digits || keep_dg;
   const int ns = nslices > keep_sl ? nslices : keep_sl;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
@@ -134,6 +143,8 @@ progress_status_t ensure_buffers(Workspace* w, int ld, bool need_x64, int nslice
     for (int i = 0; i < ns && e == cudaSuccess; ++i)
       e = cudaMalloc(&w->buf.sl[k][i], elems * sizeof(uint16_t));
   }
+  for (int d = 0; d < 5 && dg && e == cudaSuccess; ++d)
+    e = cudaMalloc(&w->buf.dg[d], elems * sizeof(uint16_t));
   int maxp = sp2::fp64_tile_count(new_ld);
   if (sp2::df64_tile_count(new_ld) > maxp) maxp = sp2::df64_tile_count(new_ld);
   const int sp = sp2::split_tile_count(new_ld);
@@ -148,6 +159,7 @@ progress_status_t ensure_buffers(Workspace* w, int ld, bool need_x64, int nslice
   w->ld_cap = new_ld;
   w->x64_cap = x64 ? new_ld : 0;
   w->slices_cap = ns;
+  w->digits_cap = dg ? new_ld : 0;
   return PROGRESS_OK;
 }
 
@@ -163,7 +175,10 @@ int slice_fmt_of(int prec, int fixed) {
 progress_status_t queue_steps(Workspace* w, const sp2::SolveParams& p, unsigned long long cond,
                               cudaStream_t s) {
   if (p.prec == PROGRESS_FP64 || is_mixed(p.prec)) {
-    if (p.df64)
+    if (p.oz) {
+      CK(sp2::launch_digits(w->buf, p.ld, s), "digits launch");
+      CK(sp2::launch_square_oz(w->buf, p.ld, p.slice_fmt, cond, s), "square_oz launch");
+    } else if (p.df64)
       CK(sp2::launch_square_df64(w->buf, p.ld, p.slice_fmt, cond, s), "square_df64 launch");
     else
       CK(sp2::launch_square_fp64(w->buf, p.ld, p.slice_fmt, cond, s), "square_fp64 launch");
@@ -175,7 +190,7 @@ progress_status_t queue_steps(Workspace* w, const sp2::SolveParams& p, unsigned 
 
 progress_status_t build_graph(Workspace* w, const sp2::SolveParams& p) {
   if (w->exec && w->g_ld == p.ld && w->g_prec == p.prec && w->g_fmt == p.slice_fmt &&
-      w->g_df == p.df64)
+      w->g_df == p.df64 && w->g_oz == p.oz)
     return PROGRESS_OK;
   free_graph(w);
   cudaGraph_t g = nullptr;
@@ -223,6 +238,7 @@ progress_status_t build_graph(Workspace* w, const sp2::SolveParams& p) {
   w->g_prec = p.prec;
   w->g_fmt = p.slice_fmt;
   w->g_df = p.df64;
+  w->g_oz = p.oz;
   return PROGRESS_OK;
 }
 
@@ -315,12 +331,16 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   if (!(tol >= 0.0)) return fail(PROGRESS_EINVAL, "tol must be >= 0");
   if (o.prec < PROGRESS_FP64 || o.prec > PROGRESS_DF64)
     return fail(PROGRESS_EINVAL, "unknown precision mode");
-  if (o.fp64_impl != 0 && o.fp64_impl != 1) return fail(PROGRESS_EINVAL, "fp64_impl must be 0 or 1");
-  // double-float FP64-accurate products: the DF64 mode, and the MIXED modes
-  // unless native FP64 is asked for
-  const int df64 = (o.prec == PROGRESS_DF64 ||
-                    ((o.prec == PROGRESS_MIXED_FP16 || o.prec == PROGRESS_MIXED_BF16) &&
-                     o.fp64_impl == 0)) ? 1 : 0;
+  if (o.fp64_impl < 0 || o.fp64_impl > 3) return fail(PROGRESS_EINVAL, "fp64_impl must be 0..3");
+  // FP64-accurate products of the MIXED modes: tensor-core digit products
+  // (3; the default up to n = 8192), double-float (2; the default above),
+  // native FP64 (1); the DF64 mode is double-float throughout
+  const bool mixed = o.prec == PROGRESS_MIXED_FP16 || o.prec == PROGRESS_MIXED_BF16;
+  if (mixed && o.fp64_impl == 3 && n > sp2::oz_max_order())
+    return fail(PROGRESS_EUNSUPPORTED, "digit products (fp64_impl 3) need n <= 8192");
+  const int oz = (mixed && (o.fp64_impl == 3 || (o.fp64_impl == 0 && n <= sp2::oz_max_order())))
+                     ? 1 : 0;
+  const int df64 = (o.prec == PROGRESS_DF64 || (mixed && o.fp64_impl != 1)) ? 1 : 0;
   if (o.prec == PROGRESS_DF64) o.prec = PROGRESS_FP64;
   // the all-split bf16 mode is the all-split mode with bf16 slices
   const bool split_bf16 = o.prec == PROGRESS_FP32_SPLIT_BF16;
@@ -358,7 +378,7 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   int fmt = slice_fmt_of(o.prec, o.slice_fixed);
   if (split_bf16) fmt = o.slice_fixed ? sp2::kBF16x3F : sp2::kBF16x3;
   const int nslices = o.prec == PROGRESS_FP64 ? 0 : sp2::fmt_slices(fmt);
-  st = ensure_buffers(w, ld, need_x64, nslices);
+  st = ensure_buffers(w, ld, need_x64, nslices, oz != 0);
   if (st != PROGRESS_OK) return st;
 
   sp2::SolveParams p;
@@ -372,6 +392,7 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   p.fp64_prefix = o.fp64_prefix;
   p.slice_fmt = fmt;
   p.df64 = df64;
+  p.oz = oz;
   p.tol = tol;
   p.emin_override = o.emin;
   p.emax_override = o.emax;

@@ -1,31 +1,38 @@
 // Batched SP2: thousands of independent dense sub-Hamiltonians of uneven size
-// (the parts of a graph-partitioned system, §VIII.B: the parts are "solved
-// for independently and concurrently") in ONE persistent kernel launch.
+// (the parts of a graph-partitioned system, §VIII.B, which are independent
+// problems solved concurrently) in ONE persistent kernel launch.
 //
-// Scheduling: one CTA per SM. A CTA takes the next instance from a device
-// work queue (instances ordered by decreasing cost n^3, so the largest start
-// first -- greedy longest-processing-time) and runs the whole SP2 solve of
-// that instance by itself: Gershgorin bounds, the X0 map, every product tile
-// of every iteration, the device-side branch/convergence decision (the same
-// rule as the dense solver) and the FP64 copy of D. No CTA ever waits for
-// another, so nothing spins on a global flag.
+// Scheduling: the grid is a set of thread-block clusters of C CTAs (C = 1, 2,
+// 4 or 8, one CTA per SM). Instances sit in a device work queue ordered by
+// decreasing size (greedy longest-processing-time). A large instance (at
+// least `share` 128-row blocks) is taken by a whole cluster: its product
+// tiles are dealt round-robin to the cluster's CTAs, the partial traces are
+// exchanged through distributed shared memory and every CTA takes the same
+// branch decision from the same sums. Fewer instances are then in flight,
+// so their operand slices stay resident in L2 across the tiles of an
+// iteration. Once the queue reaches the small instances the cluster splits
+// and each CTA takes whole instances by itself. No CTA waits on a flag in
+// global memory: cluster barriers are hardware barriers.
 //
 // Layout: every instance i is padded to m_i = round_up(n_i, 128) and stored as
-// FP16x2 operand slices in "tall" matrices of pitch P = max_i m_i: instance i
-// owns rows [row0_i, row0_i + m_i), columns [0, m_i). One TMA tensor map per
-// slice and ping-pong set therefore serves every instance.
+// operand slices (FP16x2 or BF16x3) in "tall" matrices of pitch P = max m_i:
+// instance i owns rows [row0_i, row0_i + m_i), columns [0, m_i). One TMA
+// tensor map per slice, set and operand box therefore serves every instance.
 //
-// Roles inside a CTA (256 threads), per product tile (I <= J) of an iteration:
+// Roles inside a CTA (384 threads), per product tile (128 x BN outputs):
 //   warp 0 lane 0 : TMA producer into a STAGES-deep ring (continues across
 //                   tiles, so the next tile's operands stream in during the
 //                   current tile's epilogue)
-//   warp 1 lane 0 : tcgen05.mma issuer, M = N = 128, K = 16, FP32 accumulators
-//                   acc0 (hi*hi) and acc1 (hi*lo + lo*hi) in one of two tensor
-//                   memory buffers (double-buffered across tiles)
-//   warps 4..7    : epilogue -- S = acc0 + 2^-11 acc1, X' = S or 2X - S, the
-//                   new slices of X' at (r, c) and its mirror, partial traces.
-// At the end of an iteration all threads meet, the traces are reduced and the
-// next step is decided; generic-proxy stores are fenced before the next
+//   warp 1 lane 0 : tcgen05.mma issuer, M = 128, N = BN, K = 16, FP32
+//                   accumulators in one of two tensor-memory buffers
+//                   (double-buffered across tiles)
+//   warps 4..11   : epilogue, two warps per 32-lane quarter of tensor memory
+//                   (each takes half of the tile's columns): S = X^2 from the
+//                   accumulators, X' = S or 2X - S, the new slices of X' at
+//                   (r, c) (staged through shared memory so that the stores
+//                   run along rows) and at the mirror (c, r), partial traces.
+// At the end of an iteration the traces are reduced (CTA, then cluster) and
+// the next step is decided; generic-proxy stores are fenced before the next
 // iteration's TMA reads them.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -46,42 +53,52 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;
-constexpr int TILE_BYTES = BM * BK * 2;  // one 128 x 64 slice box
-constexpr int THREADS = 256;
-constexpr int EPI_WARP0 = 4;             // warps 4..7 own tensor-memory lanes 0..127
-constexpr int TMEM_COLS = 512;           // 2 buffers x 256 columns
+constexpr int A_BYTES = BM * BK * 2;  // one 128 x 64 slice box
+constexpr int THREADS = 384;
+constexpr int NWARPS = THREADS / 32;
+constexpr int EPI_WARP0 = 4;  // warps 4..11
+constexpr int NEPI = 8;
+constexpr int MAX_CLUSTER = 8;
+constexpr int MAX_STAGES = 4;
 
-// FP16x2: acc0 (hi*hi) and acc1 (hi*lo + lo*hi, weight 2^-11) per buffer.
-// BF16x3: the slices carry their own magnitudes, so all six products go to
-// one accumulator per buffer.
-template <int F>
+template <int F, int BN>
 struct BCfg {
   static constexpr int NS = fmt_slices(F);
-  static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
-  static constexpr int STAGES = fmt_bf16(F) ? 2 : 3;
-  // epilogue staging (per epilogue warp): a 32 x 33 word plane holding the
-  // packed (slice0, slice1) of a 32 x 32 chunk, and for BF16x3 a 32 x 34
-  // half-word plane for slice 2; used to turn row-wise results into
-  // column-contiguous (coalesced) stores
-  static constexpr int EPI_A = 32 * 33;
-  static constexpr int EPI_B = 32 * 34;
-  static constexpr int EPI_BYTES = 4 * (EPI_A * 4 + (NS == 3 ? EPI_B * 2 : 0));
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = NS * (A_BYTES + B_BYTES);
+  static constexpr int STAGES = fmt_bf16(F) ? 2 : (BN == 128 ? 3 : 4);
+  // FP16x2: acc0 (hi*hi) and acc1 (hi*lo + lo*hi, weight 2^-11) per buffer;
+  // BF16x3: the slices carry their own magnitudes, one accumulator.
+  static constexpr int ACC_COLS = NS == 2 ? 2 * BN : BN;
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;
+  static constexpr int COLS_PER_WARP = BN / 2;
+  // epilogue staging per warp: 32 rows x 16 columns of packed (slice0,
+  // slice1) words (row stride 17 words) and, for BF16x3, of slice-2 half
+  // words (row stride 18)
+  static constexpr int EPI_A = 32 * 17;
+  static constexpr int EPI_B = 32 * 18;
+  static constexpr int EPI_BYTES = NEPI * (EPI_A * 4 + (NS == 3 ? EPI_B * 2 : 0));
   static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
+  static_assert(STAGES <= MAX_STAGES, "ring too deep");
+  static_assert(TMEM_COLS >= 32 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "tensor memory columns");
 };
 
 struct Maps {
-  CUtensorMap m[2][3];  // [set][slice]
+  CUtensorMap a[2][3];  // [set][slice], 64 x 128 boxes (rows of block I)
+  CUtensorMap b[2][3];  // [set][slice], 64 x BN boxes (rows of block J)
 };
 
 struct Shared {
-  State st;             // control state of the instance in flight
-  double red[2 * THREADS / 32];
-  double lo[THREADS / 32], hi[THREADS / 32];
-  uint64_t bars[2 * 3 + 5];
+  State st;  // control state of the instance in flight
+  double red[2 * NWARPS];
+  double lo[NWARPS], hi[NWARPS];
+  double xch[2][MAX_CLUSTER][4];  // cluster exchange slots [parity][rank][value]
+  uint64_t bars[2 * MAX_STAGES + 5];
   int kb_consumed;
   uint32_t tmem;
   int err;
   int inst;
+  int share;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -92,29 +109,108 @@ __device__ __forceinline__ void fence_async_global() {
   asm volatile("fence.proxy.async.global;\n" ::: "memory");
 }
 
-template <int F>
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(r));
+  return r;
+}
+
+// All threads of all CTAs of the cluster; release/acquire at cluster scope.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n"
+      "barrier.cluster.wait.acquire.aligned;\n" ::
+          : "memory");
+}
+
+__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void st_cluster_f64(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;\n" ::"r"(addr), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
+}
+
+// Product tiles of an instance with T row blocks: (I, J) with rows
+// [128 I, 128 I + 128) and columns [BN J, BN J + BN) that hold at least one
+// element on or above the diagonal, row-major.
+template <int BN>
+__device__ __forceinline__ int tile_count(int T) {
+  constexpr int R = BM / BN;
+  return R * T * (T + 1) / 2;
+}
+
+template <int BN>
+__device__ __forceinline__ void tile_of(int t, int T, int& I, int& J) {
+  if (BN == BM) {
+    tri_tile(t, T, I, J);
+    return;
+  }
+  constexpr int R = BM / BN;
+  const int C = R * T;
+  int i = 0;
+  while (t >= C - R * i) {
+    t -= C - R * i;
+    ++i;
+  }
+  I = i;
+  J = R * i + t;
+}
+
+// Thread 0 of a CTA: write (a, b, c) into slot [par][rank] of every CTA of
+// the cluster (the caller then runs cluster_sync_all()).
+__device__ __forceinline__ void xch_put(Shared& sh, int par, int rank, int G, double a, double b,
+                                        double c) {
+  const uint32_t loc = smem_u32(&sh.xch[par][rank][0]);
+  for (int r = 0; r < G; ++r) {
+    const uint32_t p = map_rank(loc, (uint32_t)r);
+    st_cluster_f64(p, a);
+    st_cluster_f64(p + 8u, b);
+    st_cluster_f64(p + 16u, c);
+  }
+}
+
+template <int F, int BN>
 __global__ void __launch_bounds__(THREADS, 1)
     batched_kernel(const __grid_constant__ Maps maps, Params prm) {
-  constexpr int NS = BCfg<F>::NS;
-  constexpr int STAGES = BCfg<F>::STAGES;
-  constexpr int STAGE_BYTES = BCfg<F>::STAGE_BYTES;
+  using Cfg = BCfg<F, BN>;
+  constexpr int NS = Cfg::NS;
+  constexpr int STAGES = Cfg::STAGES;
+  constexpr int STAGE_BYTES = Cfg::STAGE_BYTES;
+  constexpr int ACC_COLS = Cfg::ACC_COLS;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ Shared sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool epi = warp >= EPI_WARP0;
-  const int erow = threadIdx.x - EPI_WARP0 * 32;  // tile row of an epilogue thread
+  const int quarter = warp & 3;                        // tensor-memory lanes 32q .. 32q + 31
+  const int half = epi ? (warp - EPI_WARP0) >> 2 : 0;  // column half of the tile
+  const int erow = quarter * 32 + lane;                // tile row of an epilogue thread
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   unsigned char* const epi_base = smem_raw + (base - smem_u32(smem_raw)) + STAGES * STAGE_BYTES;
-  uint32_t* const epA = reinterpret_cast<uint32_t*>(epi_base) +
-                        (epi ? (warp - EPI_WARP0) * BCfg<F>::EPI_A : 0);
-  uint16_t* const epB = reinterpret_cast<uint16_t*>(epi_base + 4 * BCfg<F>::EPI_A * 4) +
-                        (epi ? (warp - EPI_WARP0) * BCfg<F>::EPI_B : 0);
+  const int ew = epi ? warp - EPI_WARP0 : 0;
+  uint32_t* const epA = reinterpret_cast<uint32_t*>(epi_base) + ew * Cfg::EPI_A;
+  uint16_t* const epB =
+      reinterpret_cast<uint16_t*>(epi_base + NEPI * Cfg::EPI_A * 4) + ew * Cfg::EPI_B;
   const uint32_t bars = smem_u32(&sh.bars[0]);
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 8u * (STAGES + s); };
-  const uint32_t tfull = bars + 8u * (2 * STAGES);      // [2] MMA -> epilogue
-  const uint32_t tempty = bars + 8u * (2 * STAGES + 2); // [2] epilogue -> MMA
+  const uint32_t tfull = bars + 8u * (2 * STAGES);          // [2] MMA -> epilogue
+  const uint32_t tempty = bars + 8u * (2 * STAGES + 2);     // [2] epilogue -> MMA
   const uint32_t drain_bar = bars + 8u * (2 * STAGES + 4);  // failure path only
+  const int G = (int)cluster_size();
+  const int rank = (int)cluster_rank();
 
   if (threadIdx.x == 0) {
     sh.err = 0;
@@ -124,31 +220,72 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull + 8u * b, 1);
-      mbar_init(tempty + 8u * b, 4);
+      mbar_init(tempty + 8u * b, NEPI);
     }
     mbar_init(drain_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(smem_u32(&sh.tmem), TMEM_COLS);
+  if (warp == 0) tmem_alloc(smem_u32(&sh.tmem), Cfg::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
   volatile int* err = &sh.err;
-  constexpr uint32_t idesc = idesc_f16(fmt_bf16(F) ? 1 : 0, BM, BM);
+  constexpr uint32_t idesc = idesc_f16(fmt_bf16(F) ? 1 : 0, BM, BN);
 
   // ring / buffer counters, each kept by the thread that uses it
   uint32_t kb_prod = 0, kb_mma = 0, tile_mma = 0, tile_epi = 0;
+  int xk = 0;             // cluster exchanges so far (the same count in every CTA of a cluster)
+  bool together = G > 1;  // the cluster still takes its instances jointly
+  if (together) cluster_sync_all();  // every CTA of the cluster is running
 
   for (;;) {
-    if (threadIdx.x == 0) {
-      const int q = atomicAdd(prm.queue, 1);
-      sh.inst = q < prm.batch ? prm.order[q] : -1;
+    // ---- next work item
+    int inst, gsz, grank;
+    if (together) {
+      cluster_sync_all();  // every CTA is done with the previous item
+      if (*err) break;     // the same in every CTA of the cluster (exchanged)
+      if (rank == 0 && threadIdx.x == 0) {
+        const int q = atomicAdd(prm.queue, 1);
+        const int i = q < prm.batch ? prm.order[q] : -1;
+        const int shr = (i >= 0 && prm.inst[i].m / BM >= prm.share) ? 1 : 0;
+        for (int r = 0; r < G; ++r) {
+          // a small instance stays with rank 0; the others then take their own
+          st_cluster_s32(map_rank(smem_u32(&sh.inst), (uint32_t)r),
+                         (r == 0 || shr || i < 0) ? i : -2);
+          st_cluster_s32(map_rank(smem_u32(&sh.share), (uint32_t)r), shr);
+        }
+      }
+      cluster_sync_all();
+      inst = sh.inst;
+      const int shr = sh.share;
+      __syncthreads();  // every thread has read sh.inst
+      if (!shr) together = false;  // the queue is sorted: no larger instance follows
+      if (inst == -2) {
+        if (threadIdx.x == 0) {
+          const int q = atomicAdd(prm.queue, 1);
+          sh.inst = q < prm.batch ? prm.order[q] : -1;
+        }
+        __syncthreads();
+        inst = sh.inst;
+      }
+      gsz = shr ? G : 1;
+      grank = shr ? rank : 0;
+    } else {
+      __syncthreads();  // every thread has read the previous sh.inst
+      if (threadIdx.x == 0) {
+        const int q = atomicAdd(prm.queue, 1);
+        sh.inst = q < prm.batch ? prm.order[q] : -1;
+      }
+      __syncthreads();
+      inst = sh.inst;
+      gsz = 1;
+      grank = 0;
+      if (*err) break;
     }
-    __syncthreads();
-    const int inst = sh.inst;
-    if (inst < 0 || *err) break;
+    if (inst < 0) break;
+    const long long c_start = clock64();
     const Instance in = prm.inst[inst];
     const int n = in.n, m = in.m, T = m / BM;
     const double* __restrict__ H = prm.H + in.offset;
@@ -160,14 +297,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     int wasted = 0;  // products of a rejected predicted run
   restart:
 
-    // ---- set-up: state, Gershgorin bounds, X0 (all threads)
+    // ---- set-up: state, Gershgorin bounds, X0 (rows dealt over the group)
     {
       unsigned int* w = reinterpret_cast<unsigned int*>(&st);
       for (int i = threadIdx.x; i < (int)(sizeof(State) / 4); i += THREADS) w[i] = 0u;
     }
     __syncthreads();
     double lo = INFINITY, hi = -INFINITY;
-    for (int r = warp; r < n; r += THREADS / 32) {
+    for (int r = grank * NWARPS + warp; r < n; r += gsz * NWARPS) {
       const double* row = H + (size_t)r * n;
       double s = 0.0;
       for (int j = lane; j < n; j += 32) s += (j == r) ? 0.0 : fabs(row[j]);
@@ -183,10 +320,25 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < THREADS / 32; ++w) {
+      for (int w = 1; w < NWARPS; ++w) {
         lo = fmin(lo, sh.lo[w]);
         hi = fmax(hi, sh.hi[w]);
       }
+      if (gsz > 1) xch_put(sh, xk & 1, grank, gsz, lo, hi, 0.0);
+    }
+    if (gsz > 1) {
+      cluster_sync_all();
+      if (threadIdx.x == 0) {
+        lo = INFINITY;
+        hi = -INFINITY;
+        for (int r = 0; r < gsz; ++r) {
+          lo = fmin(lo, sh.xch[xk & 1][r][0]);
+          hi = fmax(hi, sh.xch[xk & 1][r][1]);
+        }
+      }
+      ++xk;
+    }
+    if (threadIdx.x == 0) {
       if (!(hi > lo)) {  // zero-width enclosure: widen (as the dense solver does)
         lo -= 1.0;
         hi += 1.0;
@@ -224,7 +376,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint16_t* s1 = prm.sl[0][1];
       uint16_t* s2 = prm.sl[0][2];
       double tr = 0.0, fr = 0.0;
-      for (int r = warp; r < m; r += THREADS / 32) {
+      for (int r = grank * NWARPS + warp; r < m; r += gsz * NWARPS) {
         float trf = 0.0f, frf = 0.0f;
         const size_t g0 = (size_t)(in.row0 + r) * prm.pitch;
         for (int c = lane; c < m; c += 32) {
@@ -244,7 +396,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         tr += (double)trf;
         fr += (double)frf;
       }
+      fence_async_global();
       block_sum2(tr, fr, sh.red);
+      if (gsz > 1) {
+        if (threadIdx.x == 0) xch_put(sh, xk & 1, grank, gsz, tr, fr, 0.0);
+        cluster_sync_all();
+        if (threadIdx.x == 0) {
+          tr = 0.0;
+          fr = 0.0;
+          for (int r = 0; r < gsz; ++r) {
+            tr += sh.xch[xk & 1][r][0];
+            fr += sh.xch[xk & 1][r][1];
+          }
+        }
+        ++xk;
+      }
       if (threadIdx.x == 0) {
         st.t1 = tr;
         st.t2 = fr;
@@ -252,7 +418,6 @@ __global__ void __launch_bounds__(THREADS, 1)
         decide(&st);
       }
     }
-    fence_async_global();
     __syncthreads();
 
     // ---- SP2 iterations
@@ -260,13 +425,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int k = st.iter;
       const int bit = st.bit;
       const int src = k & 1, dst = (k + 1) & 1;
-      const int ntiles = T * (T + 1) / 2;
+      const int ntiles = tile_count<BN>(T);
       const int KB = m / BK;
       if (warp == 0) {
         if (lane == 0) {
-          for (int t = 0; t < ntiles && !*err; ++t) {
+          fence_async_global();  // slices written by the group before the barrier
+          for (int t = grank; t < ntiles && !*err; t += gsz) {
             int I, J;
-            tri_tile(t, T, I, J);
+            tile_of<BN>(t, T, I, J);
             for (int kb = 0; kb < KB; ++kb, ++kb_prod) {
               const int s = kb_prod % STAGES;
               const uint32_t ph = (kb_prod / STAGES) & 1u;
@@ -274,10 +440,10 @@ __global__ void __launch_bounds__(THREADS, 1)
               mbar_expect_tx(full_bar(s), STAGE_BYTES);
               const uint32_t sa = base + s * STAGE_BYTES;
               for (int j = 0; j < NS; ++j) {
-                tma_load_2d(sa + j * TILE_BYTES, &maps.m[src][j], kb * BK, in.row0 + I * BM,
+                tma_load_2d(sa + j * A_BYTES, &maps.a[src][j], kb * BK, (int)(in.row0 + I * BM),
                             full_bar(s));
-                tma_load_2d(sa + (NS + j) * TILE_BYTES, &maps.m[src][j], kb * BK,
-                            in.row0 + J * BM, full_bar(s));
+                tma_load_2d(sa + NS * A_BYTES + j * Cfg::B_BYTES, &maps.b[src][j], kb * BK,
+                            (int)(in.row0 + J * BN), full_bar(s));
               }
             }
           }
@@ -285,11 +451,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
       } else if (warp == 1) {
         if (lane == 0) {
-          for (int t = 0; t < ntiles && !*err; ++t, ++tile_mma) {
+          for (int t = grank; t < ntiles && !*err; t += gsz, ++tile_mma) {
             const uint32_t tb = tile_mma & 1u;
             if (!mbar_wait(tempty + 8u * tb, ((tile_mma >> 1) & 1u) ^ 1u, err)) break;
             tc_fence_after();
-            const uint32_t acc0 = tmem + 256u * tb, acc1 = acc0 + 128u;
+            const uint32_t acc0 = tmem + ACC_COLS * tb, acc1 = acc0 + BN;
             for (int kb = 0; kb < KB; ++kb, ++kb_mma) {
               const int s = kb_mma % STAGES;
               const uint32_t ph = (kb_mma / STAGES) & 1u;
@@ -299,8 +465,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               uint64_t a[NS], b[NS];
 #pragma unroll
               for (int j = 0; j < NS; ++j) {
-                a[j] = smem_desc_sw128(sa + j * TILE_BYTES);
-                b[j] = smem_desc_sw128(sa + (NS + j) * TILE_BYTES);
+                a[j] = smem_desc_sw128(sa + j * A_BYTES);
+                b[j] = smem_desc_sw128(sa + NS * A_BYTES + j * Cfg::B_BYTES);
               }
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk) {
@@ -329,7 +495,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       double tr = 0.0, fr = 0.0;
       if (epi) {
-        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const uint16_t* xs0 = prm.sl[src][0];
         const uint16_t* xs1 = prm.sl[src][1];
         const uint16_t* xs2 = prm.sl[src][2];
@@ -337,66 +503,73 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint16_t* o1 = prm.sl[dst][1];
         uint16_t* o2 = prm.sl[dst][2];
         const size_t P = prm.pitch;
-        for (int t = 0; t < ntiles; ++t, ++tile_epi) {
+        for (int t = grank; t < ntiles; t += gsz, ++tile_epi) {
           const uint32_t tb = tile_epi & 1u;
           const bool ok = mbar_wait(tfull + 8u * tb, (tile_epi >> 1) & 1u, err);
           tc_fence_after();
           int I, J;
-          tri_tile(t, T, I, J);
+          tile_of<BN>(t, T, I, J);
           const int r = I * BM + erow;  // row within the instance
+          const int rb = I * BM + quarter * 32;
           if (ok && !*err) {
 #pragma unroll 1
-            for (int ch = 0; ch < BM / 32; ++ch) {
+            for (int ch = 0; ch < Cfg::COLS_PER_WARP / 32; ++ch) {
+              const int cofs = half * Cfg::COLS_PER_WARP + ch * 32;  // column in the tile
               float v0[32], v1[32];
-              tmem_ld32(tmem + lane_base + 256u * tb + ch * 32, v0);
-              if (NS == 2) tmem_ld32(tmem + lane_base + 256u * tb + 128u + ch * 32, v1);
+              tmem_ld32(tmem + lane_base + ACC_COLS * tb + cofs, v0);
+              if (NS == 2) tmem_ld32(tmem + lane_base + ACC_COLS * tb + BN + cofs, v1);
               tmem_ld_wait();
-              const int c0 = J * BM + ch * 32;
+              const int c0 = J * BN + cofs;
               float trf = 0.0f, frf = 0.0f;
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const int c = c0 + j;
-                float x = (NS == 2) ? v0[j] + v1[j] * (1.0f / 2048.0f) : v0[j];
-                if (bit) {
-                  const size_t mi = (size_t)(in.row0 + c) * P + r;
-                  x = 2.0f * join_value<F>(xs0[mi], xs1[mi], NS == 3 ? xs2[mi] : (uint16_t)0) - x;
-                }
-                if (r <= c) {
-                  uint16_t a, b, c2;
-                  split_value_f<F>(x, a, b, c2);
-                  // (r, c) goes through the staging planes; its mirror
-                  // (c, r) is already contiguous across the warp's lanes
-                  epA[lane * 33 + j] = (uint32_t)a | ((uint32_t)b << 16);
-                  if (NS == 3) epB[lane * 34 + j] = c2;
-                  if (r == c) {
-                    trf += x;
-                    frf += x * x;
-                  } else {
-                    frf += 2.0f * x * x;
+              for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                  const int j = hh * 16 + jj;
+                  const int c = c0 + j;
+                  float x = (NS == 2) ? v0[j] + v1[j] * (1.0f / 2048.0f) : v0[j];
+                  if (bit) {
                     const size_t mi = (size_t)(in.row0 + c) * P + r;
-                    o0[mi] = a;
-                    o1[mi] = b;
-                    if (NS == 3) o2[mi] = c2;
+                    x = 2.0f * join_value<F>(xs0[mi], xs1[mi], NS == 3 ? xs2[mi] : (uint16_t)0) -
+                        x;
+                  }
+                  if (r <= c) {
+                    uint16_t a, b, c2;
+                    split_value_f<F>(x, a, b, c2);
+                    // (r, c) goes through the staging planes; its mirror
+                    // (c, r) is already contiguous across the warp's lanes
+                    epA[lane * 17 + jj] = (uint32_t)a | ((uint32_t)b << 16);
+                    if (NS == 3) epB[lane * 18 + jj] = c2;
+                    if (r == c) {
+                      trf += x;
+                      frf += x * x;
+                    } else {
+                      frf += 2.0f * x * x;
+                      const size_t mi = (size_t)(in.row0 + c) * P + r;
+                      o0[mi] = a;
+                      o1[mi] = b;
+                      if (NS == 3) o2[mi] = c2;
+                    }
                   }
                 }
+                // 16 columns x 32 rows back out, two rows per store instruction
+                __syncwarp();
+                const int cc = c0 + hh * 16 + (lane & 15);
+#pragma unroll 4
+                for (int it = 0; it < 16; ++it) {
+                  const int i = 2 * it + (lane >> 4);
+                  if (rb + i <= cc) {
+                    const uint32_t v = epA[i * 17 + (lane & 15)];
+                    const size_t dd = (size_t)(in.row0 + rb + i) * P + cc;
+                    o0[dd] = (uint16_t)(v & 0xffffu);
+                    o1[dd] = (uint16_t)(v >> 16);
+                    if (NS == 3) o2[dd] = epB[i * 18 + (lane & 15)];
+                  }
+                }
+                __syncwarp();
               }
               tr += (double)trf;
               fr += (double)frf;
-              // rows of the chunk, one per store instruction, lanes along c
-              __syncwarp();
-              const int rb = I * BM + (warp - EPI_WARP0) * 32;
-              const int cc = c0 + lane;
-#pragma unroll 4
-              for (int i = 0; i < 32; ++i) {
-                if (rb + i <= cc) {
-                  const uint32_t v = epA[i * 33 + lane];
-                  const size_t dd = (size_t)(in.row0 + rb + i) * P + cc;
-                  o0[dd] = (uint16_t)(v & 0xffffu);
-                  o1[dd] = (uint16_t)(v >> 16);
-                  if (NS == 3) o2[dd] = epB[i * 34 + lane];
-                }
-              }
-              __syncwarp();
             }
           }
           tc_fence_before();
@@ -405,7 +578,23 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         fence_async_global();  // this iteration's slices feed the next TMA reads
       }
-      block_sum2(tr, fr, sh.red);  // all threads meet here
+      block_sum2(tr, fr, sh.red);  // all threads of the CTA meet here
+      if (gsz > 1) {
+        if (threadIdx.x == 0) xch_put(sh, xk & 1, grank, gsz, tr, fr, *err ? 1.0 : 0.0);
+        cluster_sync_all();  // also publishes every CTA's slice stores to the group
+        if (threadIdx.x == 0) {
+          tr = 0.0;
+          fr = 0.0;
+          double e = 0.0;
+          for (int r = 0; r < gsz; ++r) {
+            tr += sh.xch[xk & 1][r][0];
+            fr += sh.xch[xk & 1][r][1];
+            e += sh.xch[xk & 1][r][2];
+          }
+          if (e != 0.0) *err = 1;
+        }
+        ++xk;
+      }
       if (threadIdx.x == 0) {
         if (*err) {
           st.status = PROGRESS_ETIMEOUT;
@@ -421,8 +610,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       __syncthreads();
     }
 
-    if (predicted && !*err && (st.judge_fail || st.status == PROGRESS_EBOUNDS ||
-                               st.status == PROGRESS_ENOCONV)) {
+    if (predicted && !*err &&
+        (st.judge_fail || st.status == PROGRESS_EBOUNDS || st.status == PROGRESS_ENOCONV)) {
       predicted = false;
       fell_back = true;
       wasted = st.iter;
@@ -437,12 +626,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint16_t* s1 = prm.sl[fin][1];
       const uint16_t* s2 = prm.sl[fin][2];
       double* D = prm.D + in.offset;
-      for (int idx = threadIdx.x; idx < n * n; idx += THREADS) {
+      for (int idx = grank * THREADS + threadIdx.x; idx < n * n; idx += gsz * THREADS) {
         const int r = idx / n, c = idx - r * n;
         const size_t g = (size_t)(in.row0 + r) * prm.pitch + c;
         D[idx] = (double)join_value<F>(s0[g], s1[g], NS == 3 ? s2[g] : (uint16_t)0);
       }
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == 0 && grank == 0) {
         if (prm.iters) prm.iters[inst] = st.iter;
         if (prm.fallback) prm.fallback[inst] = fell_back ? 1 : 0;
         if (prm.products) prm.products[inst] = st.iter + wasted;
@@ -461,6 +650,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           o.converged = st.converged;
           for (int b = 0; b < 4; ++b) o.bits[b] = st.bits[b];
         }
+        if (prm.cycles) prm.cycles[inst] = clock64() - c_start;
       }
     }
     __syncthreads();
@@ -482,7 +672,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
@@ -498,9 +688,78 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
+void* pick_kernel(int fmt, int tile_n, int* smem) {
+  if (fmt_bf16(fmt)) {
+    if (tile_n == 64) {
+      *smem = BCfg<kBF16x3, 64>::SMEM;
+      return reinterpret_cast<void*>(&batched_kernel<kBF16x3, 64>);
+    }
+    *smem = BCfg<kBF16x3, 128>::SMEM;
+    return reinterpret_cast<void*>(&batched_kernel<kBF16x3, 128>);
+  }
+  if (tile_n == 64) {
+    *smem = BCfg<kFP16x2, 64>::SMEM;
+    return reinterpret_cast<void*>(&batched_kernel<kFP16x2, 64>);
+  }
+  *smem = BCfg<kFP16x2, 128>::SMEM;
+  return reinterpret_cast<void*>(&batched_kernel<kFP16x2, 128>);
+}
+
+void fill_config(cudaLaunchConfig_t& lc, cudaLaunchAttribute* attr, const Config& cfg, int grid,
+                 int smem, cudaStream_t s) {
+  memset(&lc, 0, sizeof lc);
+  lc.gridDim = dim3((unsigned)grid, 1, 1);
+  lc.blockDim = dim3(THREADS, 1, 1);
+  lc.dynamicSmemBytes = (size_t)smem;
+  lc.stream = s;
+  memset(attr, 0, sizeof(cudaLaunchAttribute));
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cfg.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+}
+
 }  // namespace
 
-cudaError_t launch(const Params& prm, int grid, cudaStream_t s) {
+bool config_ok(const Config& c) {
+  return (c.tile_n == 64 || c.tile_n == 128) &&
+         (c.cluster == 1 || c.cluster == 2 || c.cluster == 4 || c.cluster == 8) && c.share >= 1;
+}
+
+int grid_size(const Config& cfg, int fmt, int batch) {
+  if (!config_ok(cfg) || batch < 1) return 0;
+  int smem = 0;
+  void* k = pick_kernel(fmt, cfg.tile_n, &smem);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  int clusters = sms / cfg.cluster;
+  if (cfg.cluster > 1) {
+    cudaLaunchConfig_t lc;
+    cudaLaunchAttribute attr[1];
+    fill_config(lc, attr, cfg, cfg.cluster, smem, nullptr);
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k, &lc) != cudaSuccess || nc < 1) {
+      cudaGetLastError();
+      return 0;
+    }
+    clusters = nc < clusters ? nc : clusters;
+  }
+  // one CTA per instance at most (rounded up to whole clusters)
+  int g = clusters * cfg.cluster;
+  if (g > batch) g = (batch + cfg.cluster - 1) / cfg.cluster * cfg.cluster;
+  return g;
+}
+
+cudaError_t launch(const Params& prm, const Config& cfg, int grid, cudaStream_t s) {
+  if (!config_ok(cfg) || grid < cfg.cluster || grid % cfg.cluster) return cudaErrorInvalidValue;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
   if (!enc) return cudaErrorNotSupported;
   const bool bf = fmt_bf16(prm.fmt);
@@ -511,24 +770,28 @@ cudaError_t launch(const Params& prm, int grid, cudaStream_t s) {
     for (int j = 0; j < ns; ++j) {
       cuuint64_t dims[2] = {(cuuint64_t)prm.pitch, (cuuint64_t)prm.total_rows};
       cuuint64_t strides[1] = {(cuuint64_t)prm.pitch * 2};
-      cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
       cuuint32_t estr[2] = {1, 1};
-      if (enc(&maps.m[k][j], bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
-              2, (void*)prm.sl[k][j], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+      for (int op = 0; op < 2; ++op) {
+        cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(op == 0 ? BM : cfg.tile_n)};
+        CUtensorMap* mp = op == 0 ? &maps.a[k][j] : &maps.b[k][j];
+        if (enc(mp, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                (void*)prm.sl[k][j], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+          return cudaErrorInvalidValue;
+      }
     }
-  if (bf) {
-    cudaFuncSetAttribute(batched_kernel<kBF16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         BCfg<kBF16x3>::SMEM);
-    batched_kernel<kBF16x3><<<grid, THREADS, BCfg<kBF16x3>::SMEM, s>>>(maps, prm);
-  } else {
-    cudaFuncSetAttribute(batched_kernel<kFP16x2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         BCfg<kFP16x2>::SMEM);
-    batched_kernel<kFP16x2><<<grid, THREADS, BCfg<kFP16x2>::SMEM, s>>>(maps, prm);
-  }
-  return cudaGetLastError();
+  int smem = 0;
+  void* k = pick_kernel(prm.fmt, cfg.tile_n, &smem);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t lc;
+  cudaLaunchAttribute attr[1];
+  fill_config(lc, attr, cfg, grid, smem, s);
+  Params p = prm;
+  p.share = cfg.share;
+  void* args[2] = {(void*)&maps, (void*)&p};
+  return cudaLaunchKernelExC(&lc, k, args);
 }
 
 }  // namespace batched

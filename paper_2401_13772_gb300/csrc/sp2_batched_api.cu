@@ -18,9 +18,37 @@
 
 namespace {
 
+using sp2::batched::Config;
 using sp2::batched::Instance;
 using sp2::batched::InstanceInfo;
 using sp2::batched::Params;
+
+// Launch configuration used when neither the caller nor the autotuner chose
+// one: 128 x 128 tiles, clusters of two CTAs sharing parts of >= 3 row blocks.
+constexpr Config kDefaultConfig = {128, 2, 3, 0};
+
+// Autotuned configurations by batch signature (device, slice format, pitch,
+// floor(log2(batch))).
+struct TuneKey {
+  int dev, fmt, pitch, lgb;
+  bool operator<(const TuneKey& o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (fmt != o.fmt) return fmt < o.fmt;
+    if (pitch != o.pitch) return pitch < o.pitch;
+    return lgb < o.lgb;
+  }
+};
+std::mutex g_tmu;
+std::map<TuneKey, Config> g_tuned;
+
+int floor_log2(int v) {
+  int l = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++l;
+  }
+  return l;
+}
 
 struct BatchWs {
   cudaStream_t cap = nullptr;
@@ -37,6 +65,8 @@ struct BatchWs {
   cudaGraphExec_t exec = nullptr;
   std::vector<Instance> last_inst;
   Params last_prm{};
+  Config last_cfg{};
+  int last_grid = 0;
   bool have_last = false;
 };
 
@@ -83,11 +113,14 @@ void drop_graph(BatchWs* w) {
 }
 
 bool same_params(const Params& a, const Params& b) { return memcmp(&a, &b, sizeof a) == 0; }
+bool same_config(const Config& a, const Config& b) {
+  return a.tile_n == b.tile_n && a.cluster == b.cluster && a.share == b.share;
+}
 
 progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t* h_offset,
                                const int32_t* h_nocc, const double* dH, double tol, double* dD,
                                int32_t* d_iters, int32_t* d_status, const progress_opts_t* opts,
-                               const progress_batch_ex_t* ex, void* stream);
+                               const progress_batch_ex_t* ex, const Config* force, void* stream);
 
 }  // namespace
 
@@ -97,7 +130,7 @@ extern "C" progress_status_t progress_sp2_batched(int32_t batch, const int32_t* 
                                                   int32_t* d_iters, int32_t* d_status,
                                                   const progress_opts_t* opts, void* stream) {
   return batched_impl(batch, h_n, h_offset, h_nocc, dH, tol, dD, d_iters, d_status, opts, nullptr,
-                      stream);
+                      nullptr, stream);
 }
 
 extern "C" progress_status_t progress_sp2_batched_ex(int32_t batch, const int32_t* h_n,
@@ -108,7 +141,7 @@ extern "C" progress_status_t progress_sp2_batched_ex(int32_t batch, const int32_
                                                      const progress_opts_t* opts,
                                                      const progress_batch_ex_t* ex, void* stream) {
   return batched_impl(batch, h_n, h_offset, h_nocc, dH, tol, dD, d_iters, d_status, opts, ex,
-                      stream);
+                      nullptr, stream);
 }
 
 namespace {
@@ -116,7 +149,7 @@ namespace {
 progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t* h_offset,
                                const int32_t* h_nocc, const double* dH, double tol, double* dD,
                                int32_t* d_iters, int32_t* d_status, const progress_opts_t* opts,
-                               const progress_batch_ex_t* ex, void* stream) {
+                               const progress_batch_ex_t* ex, const Config* force, void* stream) {
   progress_opts_t o;
   if (opts) {
     o = *opts;
@@ -155,13 +188,29 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
     rows += t.m;
     pitch = std::max(pitch, t.m);
   }
-  int dev = 0, major = 0, sms = 0;
+  int dev = 0, major = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return bcuda(e, "device query");
   if (major != 10) return bfail(PROGRESS_EUNSUPPORTED, "the batched solver needs an sm_10x GPU");
   cudaStream_t s = (cudaStream_t)stream;
+  // launch configuration: forced (autotuner), explicit (caller), tuned, default
+  Config cfg = kDefaultConfig;
+  if (force) {
+    cfg = *force;
+  } else if (ex && (ex->tile_n || ex->cluster || ex->share)) {
+    cfg.tile_n = ex->tile_n;
+    cfg.cluster = ex->cluster;
+    cfg.share = ex->share;
+  } else {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    auto it = g_tuned.find(TuneKey{dev, fmt, pitch, floor_log2(batch)});
+    if (it != g_tuned.end()) cfg = it->second;
+  }
+  if (!sp2::batched::config_ok(cfg))
+    return bfail(PROGRESS_EINVAL, "batch configuration: tile_n 64 or 128, cluster 1, 2, 4 or 8, share >= 1");
+  const int grid = sp2::batched::grid_size(cfg, fmt, batch);
+  if (grid < 1) return bcuda(cudaErrorInvalidConfiguration, "batched launch configuration");
 
   BatchWs* w = nullptr;
   {
@@ -246,7 +295,9 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
     prm.bounds_out = ex->d_bounds_out;
     prm.fallback = ex->d_fallback;
     prm.products = ex->d_products;
+    prm.cycles = reinterpret_cast<long long*>(ex->d_cycles);
   }
+  prm.share = cfg.share;
 
   const bool same_layout = w->have_last && w->last_inst.size() == inst.size() &&
                            memcmp(w->last_inst.data(), inst.data(),
@@ -260,15 +311,15 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors go out of scope
     if (e != cudaSuccess) return bcuda(e, "batched metadata upload");
   }
-  if (!(same_layout && w->exec && same_params(prm, w->last_prm))) {
+  if (!(same_layout && w->exec && same_params(prm, w->last_prm) &&
+        same_config(cfg, w->last_cfg) && grid == w->last_grid)) {
     drop_graph(w);
-    const int grid = std::min(batch, sms > 0 ? sms : 152);
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
       cudaMemsetAsync(w->queue, 0, sizeof(int32_t), w->cap);
       if (d_status) cudaMemsetAsync(d_status, 0xFF, batch * sizeof(int32_t), w->cap);
-      const cudaError_t le = sp2::batched::launch(prm, grid, w->cap);
+      const cudaError_t le = sp2::batched::launch(prm, cfg, grid, w->cap);
       e = cudaStreamEndCapture(w->cap, &g);
       if (le != cudaSuccess) e = le;
     }
@@ -280,6 +331,8 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
     }
     w->last_inst = inst;
     w->last_prm = prm;
+    w->last_cfg = cfg;
+    w->last_grid = grid;
     w->have_last = true;
   }
   e = cudaGraphLaunch(w->exec, s);
@@ -288,3 +341,115 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Autotuner
+
+extern "C" progress_status_t progress_sp2_batched_tune(
+    int32_t batch, const int32_t* h_n, const int64_t* h_offset, const int32_t* h_nocc,
+    const double* dH, double tol, double* dD, const progress_opts_t* opts, int32_t sample_stride,
+    int32_t reps, progress_batch_tune_t* out, void* stream) {
+  if (batch < 1) return bfail(PROGRESS_EINVAL, "batch must be >= 1");
+  if (!h_n || !h_offset || !h_nocc || !dH || !dD)
+    return bfail(PROGRESS_EINVAL, "NULL pointer argument");
+  if (sample_stride < 1) return bfail(PROGRESS_EINVAL, "sample_stride must be >= 1");
+  if (reps < 1 || reps > 50) return bfail(PROGRESS_EINVAL, "reps must be in [1, 50]");
+  progress_opts_t o;
+  if (opts) {
+    o = *opts;
+  } else {
+    progress_opts_default(&o);
+    o.prec = PROGRESS_FP32_SPLIT;
+  }
+  if (o.prec != PROGRESS_FP32_SPLIT && o.prec != PROGRESS_FP32_SPLIT_BF16)
+    return bfail(PROGRESS_EUNSUPPORTED,
+                 "the batched solver runs PROGRESS_FP32_SPLIT or PROGRESS_FP32_SPLIT_BF16 only");
+  const int fmt = o.prec == PROGRESS_FP32_SPLIT_BF16 ? sp2::kBF16x3 : sp2::kFP16x2;
+  int pitch = 0;
+  for (int i = 0; i < batch; ++i) {
+    if (h_n[i] < 1 || h_n[i] > 4096) return bfail(PROGRESS_EINVAL, "every n_i must be in [1, 4096]");
+    pitch = std::max(pitch, (h_n[i] + 127) / 128 * 128);
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return bcuda(e, "device query");
+  // calibration sample: every sample_stride-th instance in decreasing size
+  std::vector<int32_t> idx(batch);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return h_n[a] > h_n[b]; });
+  std::vector<int32_t> sn, snocc;
+  std::vector<int64_t> soff;
+  for (int k = 0; k < batch; k += sample_stride) {
+    sn.push_back(h_n[idx[k]]);
+    snocc.push_back(h_nocc[idx[k]]);
+    soff.push_back(h_offset[idx[k]]);
+  }
+  const int sb = (int)sn.size();
+  static const Config cands[] = {{128, 1, 1, 0}, {64, 1, 1, 0},  {128, 2, 2, 0}, {64, 2, 2, 0},
+                                 {128, 4, 3, 0}, {64, 4, 3, 0},  {128, 4, 4, 0}, {64, 4, 4, 0},
+                                 {128, 8, 4, 0}, {64, 8, 4, 0},  {128, 8, 5, 0}, {64, 8, 5, 0},
+                                 {64, 8, 3, 0}};
+  const int nc = (int)(sizeof cands / sizeof cands[0]);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  e = cudaEventCreate(&ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+  if (e != cudaSuccess) {
+    if (ev0) cudaEventDestroy(ev0);
+    return bcuda(e, "tuner events");
+  }
+  progress_batch_tune_t res;
+  memset(&res, 0, sizeof res);
+  int best = -1;
+  float best_ms = 0.0f;
+  progress_status_t st = PROGRESS_OK;
+  for (int c = 0; c < nc && st == PROGRESS_OK; ++c) {
+    res.cand[c][0] = cands[c].tile_n;
+    res.cand[c][1] = cands[c].cluster;
+    res.cand[c][2] = cands[c].share;
+    res.ms[c] = -1.0f;
+    res.ncand = c + 1;
+    if (sp2::batched::grid_size(cands[c], fmt, sb) < 1) continue;  // not launchable here
+    st = batched_impl(sb, sn.data(), soff.data(), snocc.data(), dH, tol, dD, nullptr, nullptr, &o,
+                      nullptr, &cands[c], stream);
+    if (st != PROGRESS_OK) break;
+    std::vector<float> t;
+    for (int r = 0; r < reps && st == PROGRESS_OK; ++r) {
+      e = cudaEventRecord(ev0, s);
+      if (e == cudaSuccess) {
+        st = batched_impl(sb, sn.data(), soff.data(), snocc.data(), dH, tol, dD, nullptr, nullptr,
+                          &o, nullptr, &cands[c], stream);
+        if (st != PROGRESS_OK) break;
+        e = cudaEventRecord(ev1, s);
+      }
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+      if (e != cudaSuccess) {
+        st = bcuda(e, "tuner timing");
+        break;
+      }
+      t.push_back(ms);
+    }
+    if (st != PROGRESS_OK) break;
+    std::sort(t.begin(), t.end());
+    res.ms[c] = t[t.size() / 2];
+    if (best < 0 || res.ms[c] < best_ms) {
+      best = c;
+      best_ms = res.ms[c];
+    }
+  }
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (st != PROGRESS_OK) return st;
+  if (best < 0) return bfail(PROGRESS_EUNSUPPORTED, "no batched launch configuration fits this GPU");
+  res.tile_n = cands[best].tile_n;
+  res.cluster = cands[best].cluster;
+  res.share = cands[best].share;
+  {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_tuned[TuneKey{dev, fmt, pitch, floor_log2(batch)}] = cands[best];
+  }
+  if (out) *out = res;
+  return PROGRESS_OK;
+}

@@ -126,6 +126,7 @@ __device__ inline void decide(State* st) {
   }
   int phase = st->phase;
   bool stalled = false;
+  bool refine_floor = false;
   if (st->prec == PROGRESS_FP64) {
     phase = kPhaseFP64;
   } else {
@@ -156,7 +157,21 @@ __device__ inline void decide(State* st) {
       // MIXED: leave room for the FP64 refinement before maxiter.
       if (st->prec != PROGRESS_FP32_SPLIT && k >= st->maxiter - 10) stalled = true;
     }
-    if (stalled && st->prec != PROGRESS_FP32_SPLIT) phase = kPhaseRefine;  // MIXED
+    if (stalled && st->prec != PROGRESS_FP32_SPLIT) {  // MIXED: start the refinement
+      phase = kPhaseRefine;
+      st->best_split_idem = idem;
+      st->split_stall = 0;
+    } else if (phase == kPhaseRefine) {
+      // Refinement converges quadratically down to the round-off floor of
+      // its FP64-accurate products (about n times their absolute error):
+      // two steps that do not halve the error mean the floor is reached.
+      if (idem < st->best_split_idem * 0.5) {
+        st->best_split_idem = idem;
+        st->split_stall = 0;
+      } else if (++st->split_stall >= 2 && idem < 1e-6 * n) {
+        refine_floor = true;
+      }
+    }
   }
   st->phase = phase;
   if (stalled && st->prec == PROGRESS_FP32_SPLIT) {
@@ -166,7 +181,8 @@ __device__ inline void decide(State* st) {
     return;
   }
   // Convergence is tested in FP64-accurate phases and in the all-split mode.
-  if ((phase != kPhaseSplit || st->prec == PROGRESS_FP32_SPLIT) && idem < st->tol) {
+  if (((phase != kPhaseSplit || st->prec == PROGRESS_FP32_SPLIT) && idem < st->tol) ||
+      refine_floor) {
     st->converged = 1;
     st->done = 1;
     return;

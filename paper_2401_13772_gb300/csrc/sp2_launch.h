@@ -14,6 +14,7 @@ struct DevBuffers {
   State* st;
   double* x64[2];        // FP64 ping-pong iterates, ld x ld
   uint16_t* sl[2][3];    // slice ping-pong sets, ld x ld each
+  uint16_t* dg[5];       // BF16 fixed-point digits of the iterate (digit products), ld x ld
   double* partials;      // per-CTA partial traces (2 doubles per CTA)
   int max_partials;
 };
@@ -28,6 +29,7 @@ struct SolveParams {
   int fp64_prefix;
   int slice_fmt;
   int df64;  // FP64-accurate products in double-float (FP64 buffers hold hi/lo planes)
+  int oz;    // ... computed as exact digit products on the tensor cores (needs df64)
   double tol;
   double emin_override, emax_override;
 };
@@ -46,6 +48,13 @@ cudaError_t launch_square_fp64(const DevBuffers& b, int ld, int slice_fmt,
 cudaError_t launch_square_df64(const DevBuffers& b, int ld, int slice_fmt,
                                unsigned long long cond_handle, cudaStream_t s);
 int df64_tile_count(int ld);
+// Digits of the iterate, then one FP64-accurate product from exact BF16 digit
+// products on the tensor cores (both no-ops unless the next product is
+// FP64-accurate); ld <= oz_max_order().
+cudaError_t launch_digits(const DevBuffers& b, int ld, cudaStream_t s);
+cudaError_t launch_square_oz(const DevBuffers& b, int ld, int slice_fmt,
+                             unsigned long long cond_handle, cudaStream_t s);
+int oz_max_order();
 // One split-precision tcgen05 product step (no-op unless the next product is split).
 cudaError_t launch_square_split(const DevBuffers& b, const SolveParams& p,
                                 unsigned long long cond_handle, cudaStream_t s);

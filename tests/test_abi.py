@@ -52,6 +52,28 @@ def test_struct_sizes_match_header_layout():
     # progress_info_t: 6 int32, 4 double, 4 uint64
     assert ctypes.sizeof(_lib.Info) == 6 * 4 + 4 * 8 + 4 * 8
     assert _lib.Info.emin.offset == 24 and _lib.Info.bits.offset == 56
+    # progress_batch_ex_t: 8 pointer/double slots, 4 int32 (configuration), 1 pointer
+    assert ctypes.sizeof(_lib.BatchEx) == 8 * 8 + 4 * 4 + 8
+    assert _lib.BatchEx.tile_n.offset == 64 and _lib.BatchEx.d_cycles.offset == 80
+    # progress_batch_tune_t: 4 int32, int32 cand[16][3], float ms[16]
+    assert ctypes.sizeof(_lib.BatchTune) == 4 * 4 + 16 * 3 * 4 + 16 * 4
+    assert _lib.BatchTune.ms.offset == 16 + 16 * 3 * 4
+
+
+def test_batched_argument_errors(lib):
+    from paper_2401_13772_gb300 import _lib
+    P = ctypes.c_void_p
+    n = (ctypes.c_int32 * 2)(64, 5000)
+    off = (ctypes.c_int64 * 2)(0, 4096)
+    nocc = (ctypes.c_int32 * 2)(32, 10)
+    assert lib.progress_sp2_batched(2, n, off, nocc, P(16), 1e-9, P(32), None, None, None,
+                                    None) == _lib.EINVAL
+    assert b"n_i" in lib.progress_last_error()
+    tune = _lib.BatchTune()
+    assert lib.progress_sp2_batched_tune(2, n, off, nocc, P(16), 1e-9, P(32), None, 0, 3,
+                                         ctypes.byref(tune), None) == _lib.EINVAL
+    assert lib.progress_sp2_batched_tune(2, n, off, nocc, P(16), 1e-9, P(32), None, 1, 3,
+                                         ctypes.byref(tune), None) == _lib.EINVAL
 
 
 def test_defaults_and_version(lib):

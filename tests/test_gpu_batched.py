@@ -133,3 +133,90 @@ def test_batched_rejects_bad_arguments(pkg):
                                   ctypes.c_void_p(no.ctypes.data), ctypes.c_void_p(8), 1e-9,
                                   ctypes.c_void_p(16), None, None, ctypes.byref(o), None)
     assert st == _lib.EUNSUPPORTED
+
+
+# Launch configurations of the batched kernel: (tile_n, cluster, share). With
+# share = 1 every instance is solved by a whole cluster, so with cluster 4 the
+# CTAs of a one-tile instance have no tile to compute and only join the
+# exchanges.
+CONFIGS = [(128, 1, 1), (64, 1, 1), (128, 2, 1), (128, 2, 3), (128, 4, 2), (64, 4, 1),
+           (64, 2, 2), (64, 8, 1), (128, 8, 3)]
+
+
+@pytest.fixture(scope="module")
+def mixed_batch():
+    # sizes spanning 1..4 row blocks of 128 (ragged), Nocc = n/2 and one odd filling
+    sites = [16, 17, 31, 32, 33, 50, 64, 65, 80, 100, 120, 128, 40, 24]
+    mats, noccs = [], []
+    for i, s in enumerate(sites):
+        H, nocc = batch_instance(500 + i, s)
+        mats.append(H)
+        noccs.append(nocc if i != 5 else nocc - 7)
+    refs = [oracle.sp2_plain(H, k, 1e-10)["D"] for H, k in zip(mats, noccs)]
+    gates = [gate(H, k, "fp32_split") for H, k in zip(mats, noccs)]
+    return mats, noccs, refs, gates
+
+
+def run_cfg(pkg, mats, noccs, cfg, prec="fp32_split", cycles=False):
+    import torch
+    packed, n, offsets = pkg.pack_batch(mats)
+    Hd = torch.from_numpy(packed).to("cuda:0")
+    res = pkg.sp2_batched(Hd, n, offsets, noccs, 1e-10, prec=prec, config=cfg, cycles=cycles)
+    torch.cuda.synchronize()
+    Dh = res[0].cpu().numpy()
+    outs = [Dh[o:o + k * k].reshape(k, k) for o, k in zip(offsets, n)]
+    return (outs,) + tuple(r.cpu().numpy() for r in res[1:])
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_batched_launch_configs_match_oracle(pkg, mixed_batch, cfg):
+    mats, noccs, refs, gates = mixed_batch
+    outs, iters, status = run_cfg(pkg, mats, noccs, cfg)
+    for H, k, D, ref, g, st in zip(mats, noccs, outs, refs, gates, status):
+        assert st == 0, (cfg, H.shape[0], st)
+        err = float(np.abs(D - ref).max())
+        assert err <= g, (cfg, H.shape[0], err, g)
+        assert abs(np.trace(D) - k) <= 4e-6 * H.shape[0]
+
+
+def test_batched_configs_agree_and_report_cycles(pkg, mixed_batch):
+    mats, noccs, refs, gates = mixed_batch
+    base, it0, st0, cyc0 = run_cfg(pkg, mats, noccs, (128, 1, 1), cycles=True)
+    assert (cyc0 > 0).all()
+    for cfg in [(64, 2, 1), (128, 4, 1)]:
+        outs, it, st, cyc = run_cfg(pkg, mats, noccs, cfg, cycles=True)
+        assert (cyc > 0).all()
+        assert np.abs(it.astype(int) - it0.astype(int)).max() <= 2
+        for D0, D, g in zip(base, outs, gates):
+            assert float(np.abs(D - D0).max()) <= 2 * g
+    # the same configuration twice: bit-identical
+    again, it1, st1 = run_cfg(pkg, mats, noccs, (128, 4, 1))[:3]
+    outs, it2, st2 = run_cfg(pkg, mats, noccs, (128, 4, 1))[:3]
+    assert all(np.array_equal(a, b) for a, b in zip(again, outs))
+
+
+def test_batched_bf16_shared_instances(pkg, mixed_batch):
+    mats, noccs, refs, gates = mixed_batch
+    outs, iters, status = run_cfg(pkg, mats, noccs, (128, 2, 1), prec="fp32_split_bf16")
+    for H, k, D, ref, st in zip(mats, noccs, outs, refs, status):
+        assert st == 0
+        assert float(np.abs(D - ref).max()) <= gate(H, k, "fp32_split_bf16")
+
+
+def test_batched_autotuner(pkg, mixed_batch):
+    import torch
+    mats, noccs, refs, gates = mixed_batch
+    packed, n, offsets = pkg.pack_batch(mats)
+    Hd = torch.from_numpy(packed).to("cuda:0")
+    rep = pkg.batched_tune(Hd, n, offsets, noccs, 1e-10, sample_stride=2, reps=1)
+    timed = [c for c in rep["candidates"] if c["ms"] > 0]
+    assert len(timed) >= 2
+    best = min(timed, key=lambda c: c["ms"])
+    assert (rep["tile_n"], rep["cluster"], rep["share"]) == (best["tile_n"], best["cluster"],
+                                                            best["share"])
+    # later calls with the same batch signature run the tuned configuration
+    outs, iters, status = run_batch(pkg, mats, noccs)
+    for H, k, D, ref, g, st in zip(mats, noccs, outs, refs, gates, status):
+        assert st == 0 and float(np.abs(D - ref).max()) <= g
+    with pytest.raises(Exception):
+        pkg.sp2_batched(Hd, n, offsets, noccs, 1e-10, config=(96, 1, 1))

@@ -185,11 +185,42 @@ def test_df64_products_match_plain_sp2(pkg):
         assert np.abs(host(D) - Dref).max() <= TOL_FP64
 
 
+def test_digit_products_match_plain_sp2(pkg):
+    """FP64-accurate products as exact BF16 digit products on the tensor cores
+    (fp64_impl 3): with a prefix longer than the run, every product is one of
+    them; the iterates track the FP64 oracle's (digits carry 2^-44 absolute,
+    the products ~2^-40)."""
+    for sites, seed in ((75, 5), (32, 3)):  # n = 300 (ragged, 3 row blocks), 128 (one tile)
+        H, nocc = cube_hamiltonian(sites, seed)
+        for k in (1, 2, 6, 14):
+            D, info = pkg.sp2_dense_ex(dev(H), nocc, 0.0, prec="mixed_fp16", fp64_impl=3,
+                                       fp64_prefix=60, maxiter=k, raise_on_status=False)
+            ref = oracle.sp2_plain(H, nocc, 0.0, stop_after=k)
+            assert info["iters"] == k and info["bits"] == ref["bits"]
+            assert np.abs(host(D) - ref["D"]).max() <= 1e-10, (sites, k)
+            assert abs(info["trace"] - ref["t1"][-1]) <= 1e-8
+
+
+def test_digit_product_mixed_solve_meets_mixed_gate(pkg):
+    """n = 1000 (8 chunks of 128 k for the exact G2 drain): the whole mixed
+    solve with digit-product prefix and refinement."""
+    H, nocc = cube_hamiltonian(250, 4)
+    w, V = oracle.jacobi_eigh(H)
+    Dref, _ = oracle.density_projector(w, V, nocc)
+    for fmt in ("mixed_fp16", "mixed_bf16"):
+        D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-10, prec=fmt, fp64_impl=3, fp64_prefix=8)
+        assert info["status"] == "OK" and info["converged"], info
+        Dn = host(D)
+        assert np.abs(Dn - Dref).max() <= 1e-5
+        assert abs(np.trace(Dn) - nocc) <= 1e-8
+        assert info["phase_iters"][0] == 8 and info["phase_iters"][2] >= 1
+
+
 def test_mixed_with_native_and_double_float_fp64_phases(pkg):
     H, nocc = cube_hamiltonian(250, 4)
     w, V = oracle.jacobi_eigh(H)
     Dref, _ = oracle.density_projector(w, V, nocc)
-    for impl in (0, 1):
+    for impl in (0, 1, 2):  # default (digit products here), native FP64, double-float
         D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-10, prec="mixed_fp16", fp64_impl=impl)
         assert info["status"] == "OK" and info["converged"]
         Dn = host(D)
