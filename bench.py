@@ -237,17 +237,33 @@ def run_reference(args):
 
 def run_batched(args):
     """Batched workload: `--batch` cube parts of U{16..192} sites (n = 64..768),
-    Nocc = n/2, one persistent launch per step."""
+    Nocc = n/2, one persistent launch per step. Under torchrun the parts are
+    sharded over the ranks (greedy LPT on n^3, no collective on the data path)
+    and the step time is the maximum over ranks."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     import oracle
     import paper_2401_13772_gb300 as pkg
     from paper_2401_13772_gb300.build import build
+    from paper_2401_13772_gb300.sharding import max_over_ranks, shard_parts
     from workloads import batch_packed, batch_sizes
-    sites = batch_sizes(args.batch, 0)
-    packed, n, offsets, nocc = batch_packed(sites, 1000)
-    build()
-    dev = torch.device("cuda", 0)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    all_sites = batch_sizes(args.batch, 0)
+    mine = np.array(shard_parts(4 * all_sites, world, rank) if world > 1 else
+                    range(args.batch), dtype=np.int64)
+    sites = all_sites[mine]
+    packed, n, offsets, nocc = batch_packed(sites, 1000, index=mine)
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
     Hh = torch.from_numpy(packed).pin_memory()
     H = Hh.to(dev)
     D = torch.empty_like(H)
@@ -267,14 +283,36 @@ def run_batched(args):
     K = args.steps
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
     clocks = ClockSampler()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     clocks.start()
     for i in range(K):
         ev[2 * i].record(stream)
         pkg.sp2_batched(H, n, offsets, nocc, 1e-10, D_packed=D, prec=args.batch_prec)
         ev[2 * i + 1].record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clk = clocks.stop()
-    sec = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(K)) / K / 1e3
+    sec_local = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(K)) / K / 1e3
+    sec = max_over_ranks(sec_local, device=dev)  # the whole job ends with its slowest rank
+    # end to end through the C ABI with host buffers (H in, D out), every rank
+    Dh_pin = torch.empty_like(Hh).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    H.copy_(Hh, non_blocking=True)
+    pkg.sp2_batched(H, n, offsets, nocc, 1e-10, D_packed=D, prec=args.batch_prec)
+    Dh_pin.copy_(D, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_sec = max_over_ranks(e0.elapsed_time(e1) / 1e3, device=dev)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
     it = iters.cpu().numpy()
     st = status.cpu().numpy()
     # per-part SM cycles of one more launch, by row blocks of 128 (outside the timing)
@@ -287,24 +325,23 @@ def run_batched(args):
                           "share_of_cycles": round(float(cyc[blocks == b].sum() / cyc.sum()), 3)}
                  for b in np.unique(blocks)}
     nn = n.astype(np.float64)
-    flops = float(np.sum(it * nn * nn * (nn + 1)))
+    flops = float(np.sum(it * nn * nn * (nn + 1)))  # this GPU's launch
     peaks, src = load_peaks()
     peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
-    ach = flops / sec / 1e12
+    ach = flops / sec_local / 1e12
     # a loop of plain per-instance solves (dense FP32-split API), subsample
-    sub = np.linspace(0, args.batch - 1, 100).astype(int)
+    sub = np.linspace(0, len(n) - 1, 100).astype(int)
     mats = [torch.from_numpy(packed[offsets[i]:offsets[i] + int(n[i]) ** 2].reshape(
         int(n[i]), int(n[i]))).to(dev) for i in sub]
     for m_, i in zip(mats[:3], sub[:3]):
         pkg.sp2_dense_ex(m_, int(nocc[i]), 1e-10, prec="fp32_split")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     for m_, i in zip(mats, sub):
         pkg.sp2_dense_ex(m_, int(nocc[i]), 1e-10, info=False, prec="fp32_split")
     e1.record(stream)
     torch.cuda.synchronize()
-    loop_sec = e0.elapsed_time(e1) / 1e3 * args.batch / len(sub)
+    loop_sec = e0.elapsed_time(e1) / 1e3 * args.batch / len(sub) / world
     # accuracy on a sample against the oracle
     Dh = D.cpu().numpy()
     errs = []
@@ -321,17 +358,7 @@ def run_batched(args):
         oracle.sp2_plain(packed[offsets[i]:offsets[i] + k * k].reshape(k, k), int(nocc[i]),
                          1e-10)
     cpu_sec = (time.perf_counter() - t0) * args.batch / 20
-    # end to end through the C ABI with host buffers
-    Dh_pin = torch.empty_like(Hh).pin_memory()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    H.copy_(Hh, non_blocking=True)
-    pkg.sp2_batched(H, n, offsets, nocc, 1e-10, D_packed=D, prec=args.batch_prec)
-    Dh_pin.copy_(D, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_sec = e0.elapsed_time(e1) / 1e3
-    line = {"metric": METRIC, "value": args.batch / sec, "unit": UNIT, "n_gpus": 1,
+    line = {"metric": METRIC, "value": args.batch / sec, "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": sec * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": ("f16x2 split, f32 accumulate" if args.batch_prec == "fp32_split"
@@ -339,14 +366,14 @@ def run_batched(args):
             "data": "synthetic",
             "config": {"workload": f"{args.batch} random-cube parts, U{{16..192}} sites x 4 "
                                    f"orbitals (n = 64..768), Nocc = n/2, seeds 1000+i",
-                       "prec": args.batch_prec, "tol": 1e-10,
+                       "prec": args.batch_prec, "tol": 1e-10, "parallelism": "one GPU",
                        "l2": "inputs (about 7 GB) far larger than L2"},
             "iters_mean": float(it.mean()), "status_ok": int((st == 0).sum()),
             "tflops_algorithmic": ach,
             "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak, "traffic": None, "kernel": "batched_kernel",
                          "peak_source": f"fp16/bf16 dense, {src} burst",
-                         "flops_per_launch": flops, "avg_launch_ms": sec * 1e3},
+                         "flops_per_launch": flops, "avg_launch_ms": sec_local * 1e3},
             "loop_baseline": {"value": args.batch / loop_sec, "unit": UNIT,
                               "what": "per-instance dense FP32-split solves in a loop "
                                       "(100-instance subsample, scaled)"},
@@ -361,6 +388,9 @@ def run_batched(args):
             "gpu_launches": K, "clocks": clk,
             "launch_config": tune if tune is not None else "library default",
             "cycles_by_row_blocks": by_blocks}
+    if world > 1:
+        line["config"]["parallelism"] = f"parts sharded over {world} ranks (LPT on n^3)"
+        dist.destroy_process_group()
     print(json.dumps(line), flush=True)
 
 
@@ -552,9 +582,8 @@ def main():
     loop_ms = [lp_s[i].elapsed_time(lp_e[i]) for i in range(K)]
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_2401_13772_gb300.sharding import max_over_ranks
+        total_ms = max_over_ranks(total_ms, device=dev)
     value = world * K / (total_ms / 1e3)
     ms_per_step = total_ms / K
 

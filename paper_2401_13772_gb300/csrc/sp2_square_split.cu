@@ -20,14 +20,18 @@
 //                      chain of same-sign products (the diagonal of X*X) that
 //                      truncation becomes a measurable bias; short chains
 //                      summed with round-to-nearest adds remove it.
-//   warps 4..7       : drain -- each thread owns one tensor-memory lane (a
-//                      tile row); it adds every finished acc0 chunk into 128
-//                      FP32 registers and frees the buffer (mbarrier), then
+//   warps 4..11      : drain -- two warps per 32-lane quarter of tensor
+//                      memory, each thread owns one lane (a tile row) and 64
+//                      of the tile's columns; it adds every finished acc0
+//                      chunk into 64 FP32 registers and frees the buffer
+//                      (mbarrier), then
 //                      runs the epilogue: S = w0 sum0 + w1 acc1 (+ w2 acc2)
 //                      in FP32 (no FP64 arithmetic: it is slow on this part),
 //                      the SP2 branch of §IV.A chosen on the device (X' = S or
-//                      2X - S), the new slices of X' at (r, c) and at the
-//                      mirror (c, r), FP64 X' when the precision schedule may
+//                      2X - S), the new slices of X' at (r, c) (staged
+//                      through the then idle operand ring so that the stores
+//                      run along rows) and at the mirror (c, r), FP64 X' when
+//                      the precision schedule may
 //                      leave the split phase next, and the partial traces
 //                      Tr X', ||X'||_F^2 (FP32 over 32 columns, folded into
 //                      FP64 per chunk).
@@ -52,8 +56,10 @@ constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 64;                         // 16-bit elements = 128 B rows
 constexpr int TILE_BYTES = BM * BK * 2;        // one 128 x 64 slice box (16 KB)
-constexpr int THREADS = 256;       // warp 0 TMA, warp 1 MMA, warps 4..7 drain + epilogue
-constexpr int DRAIN_WARPS = 4;     // one per 32-lane quarter of tensor memory
+constexpr int THREADS = 384;       // warp 0 TMA, warp 1 MMA, warps 4..11 drain + epilogue
+constexpr int DRAIN_WARPS = 8;     // two per 32-lane quarter of tensor memory
+constexpr int DRAIN_WARP0 = 4;
+constexpr int DCOLS = BN / 2;      // columns per drain thread
 constexpr int CHUNK = 4;           // k-blocks per leading-group accumulation chunk
 constexpr int TMEM_COLS = 512;     // acc0 x2 | acc1 | acc2, 128 columns each
 
@@ -71,28 +77,6 @@ struct TensorMaps {
 };
 
 using namespace tc;
-
-template <int F>
-__device__ __forceinline__ void pack_store_row(uint16_t* const* dst, size_t off, const float* x) {
-  // 32 consecutive values of one row -> slices, 16-byte stores
-  uint32_t w[3][16];
-#pragma unroll
-  for (int j = 0; j < 32; j += 2) {
-    uint16_t a0, b0, c0, a1, b1, c1;
-    split_value_f<F>(x[j], a0, b0, c0);
-    split_value_f<F>(x[j + 1], a1, b1, c1);
-    w[0][j / 2] = (uint32_t)a0 | ((uint32_t)a1 << 16);
-    w[1][j / 2] = (uint32_t)b0 | ((uint32_t)b1 << 16);
-    w[2][j / 2] = (uint32_t)c0 | ((uint32_t)c1 << 16);
-  }
-#pragma unroll
-  for (int s = 0; s < Cfg<F>::NS; ++s) {
-    uint4* p = reinterpret_cast<uint4*>(dst[s] + off);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      p[q] = make_uint4(w[s][4 * q], w[s][4 * q + 1], w[s][4 * q + 2], w[s][4 * q + 3]);
-  }
-}
 
 template <int F>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -240,23 +224,26 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
   }
 
-  // ---- drain warps: thread owns TMEM lane = tile row, sums the leading-group
-  // chunks with round-to-nearest FP32 adds, then runs the epilogue.
-  const bool drain = warp >= THREADS / 32 - DRAIN_WARPS;
-  const int row = threadIdx.x - (THREADS - 128);
-  const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  float sum0[BN];
+  // ---- drain warps: thread owns TMEM lane = tile row and DCOLS columns, sums
+  // the leading-group chunks with round-to-nearest FP32 adds, then runs the
+  // epilogue.
+  const bool drain = warp >= DRAIN_WARP0;
+  const int quarter = warp & 3;
+  const int half = drain ? (warp - DRAIN_WARP0) >> 2 : 0;
+  const int row = quarter * 32 + lane;
+  const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+  float sum0[DCOLS];
 #pragma unroll
-  for (int j = 0; j < BN; ++j) sum0[j] = 0.0f;
+  for (int j = 0; j < DCOLS; ++j) sum0[j] = 0.0f;
   if (drain) {
     for (int c = 0; c < NC; ++c) {
       const int cb = c & 1;
       if (!mbar_wait(chunk_full + 8u * cb, (uint32_t)(c >> 1) & 1u, err)) break;
       tc_fence_after();
 #pragma unroll
-      for (int q = 0; q < BN / 32; ++q) {
+      for (int q = 0; q < DCOLS / 32; ++q) {
         float v[32];
-        tmem_ld32(lane_addr + 128u * cb + q * 32, v);
+        tmem_ld32(lane_addr + 128u * cb + half * DCOLS + q * 32, v);
         tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 32; ++j) sum0[q * 32 + j] += v[j];
@@ -276,62 +263,93 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (drain && ok && *err == 0) {
     using W = SliceWeights<F>;
     const int r = row_a + row;
-    const uint16_t* xs0 = buf.sl[src][0];
-    const uint16_t* xs1 = buf.sl[src][1];
-    const uint16_t* xs2 = buf.sl[src][2];
-    uint16_t* out[3] = {buf.sl[dst][0], buf.sl[dst][1], buf.sl[dst][2]};
-    double* out64 = buf.x64[dst];
+    // (selects, not a runtime index into the parameter arrays)
+    const bool odd = src != 0;
+    const uint16_t* xs0 = odd ? buf.sl[1][0] : buf.sl[0][0];
+    const uint16_t* xs1 = odd ? buf.sl[1][1] : buf.sl[0][1];
+    const uint16_t* xs2 = odd ? buf.sl[1][2] : buf.sl[0][2];
+    uint16_t* const out0 = odd ? buf.sl[0][0] : buf.sl[1][0];
+    uint16_t* const out1 = odd ? buf.sl[0][1] : buf.sl[1][1];
+    uint16_t* const out2 = odd ? buf.sl[0][2] : buf.sl[1][2];
+    double* out64 = odd ? buf.x64[0] : buf.x64[1];
     // FP64-accurate phases read the next iterate from the FP64 buffer: as
     // doubles, or as double-float planes (hi = x, lo = 0)
     const bool df = st->df64 != 0;
     float* out_hi = reinterpret_cast<float*>(out64);
     float* out_lo = out_hi + (size_t)ld * ld;
-    const bool diag = (I == J);
+    // staging of the (r, c) slice stores in the idle operand ring: per warp
+    // 32 rows x 32 columns of packed (slice0 | slice1 << 16) words (row
+    // stride 33) and, for BF16x3, of slice-2 half words (row stride 34)
+    uint32_t* stA = reinterpret_cast<uint32_t*>(smem_raw + (base - smem_u32(smem_raw))) +
+                    (warp - DRAIN_WARP0) * (32 * 33);
+    uint16_t* stB = reinterpret_cast<uint16_t*>(smem_raw + (base - smem_u32(smem_raw)) +
+                                                DRAIN_WARPS * 32 * 33 * 4) +
+                    (warp - DRAIN_WARP0) * (32 * 34);
+    const int rb = row_a + quarter * 32;
 #pragma unroll
-    for (int ch = 0; ch < BN / 32; ++ch) {
-      float v0[32], v1[32];
-      tmem_ld32(lane_addr + 256 + ch * 32, v1);
-      tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v0[j] = sum0[ch * 32 + j] * W::w0 + v1[j] * W::w1;
-      if (fmt_bf16(F)) {
-        tmem_ld32(lane_addr + 384 + ch * 32, v1);
-        tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v0[j] += v1[j] * W::w2;
-      }
-      const int c0 = row_b + ch * 32;
+    for (int ch = 0; ch < DCOLS / 32; ++ch) {
+      const int col = half * DCOLS + ch * 32;  // column in the tile
+      const int c0 = row_b + col;
       float trf = 0.0f, frf = 0.0f;  // chunk partials (FP32), folded into FP64 below
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = c0 + j;
-        float x = v0[j];
+      for (int hh = 0; hh < 2; ++hh) {
+        const int cs = c0 + hh * 16;
+        // the mirror values of X for 2X - X^2 do not depend on the products:
+        // load them before waiting on tensor memory (packed slice0 | slice1)
+        uint32_t m01[16], m2[16];
         if (bit) {
-          const size_t m = (size_t)c * ld + r;  // X is symmetric: read the mirror (coalesced)
-          const float xo =
-              join_value<F>(xs0[m], xs1[m], fmt_bf16(F) ? xs2[m] : (uint16_t)0);
-          x = 2.0f * xo - x;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const size_t m = (size_t)(cs + j) * ld + r;  // X is symmetric: coalesced
+            m01[j] = (uint32_t)xs0[m] | ((uint32_t)xs1[m] << 16);
+            m2[j] = fmt_bf16(F) ? (uint32_t)xs2[m] : 0u;
+          }
         }
-        v0[j] = x;
-        if (r <= c) {
-          if (r == c) {
-            trf += x;
-            frf += x * x;
-          } else {
-            frf += 2.0f * x * x;
-            // mirror (c, r): consecutive threads write consecutive r
-            const size_t m = (size_t)c * ld + r;
-            uint16_t a, b2, c2;
-            split_value_f<F>(x, a, b2, c2);
-            out[0][m] = a;
-            out[1][m] = b2;
-            if (fmt_bf16(F)) out[2][m] = c2;
-            if (want_fp64) {
+        uint32_t u1[16], u2[16];
+        tmem_ld16(lane_addr + 256 + col + hh * 16, u1);
+        if (fmt_bf16(F)) tmem_ld16(lane_addr + 384 + col + hh * 16, u2);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int jj = hh * 16 + j;  // column within the 32-column chunk
+          const int c = cs + j;
+          float x = sum0[ch * 32 + jj] * W::w0 + __uint_as_float(u1[j]) * W::w1;
+          if (fmt_bf16(F)) x += __uint_as_float(u2[j]) * W::w2;
+          if (bit)
+            x = 2.0f * join_value<F>((uint16_t)(m01[j] & 0xffffu), (uint16_t)(m01[j] >> 16),
+                                     (uint16_t)m2[j]) -
+                x;
+          uint16_t a, b2, c2;
+          split_value_f<F>(x, a, b2, c2);
+          stA[lane * 33 + jj] = (uint32_t)a | ((uint32_t)b2 << 16);
+          if (fmt_bf16(F)) stB[lane * 34 + jj] = c2;
+          if (r <= c) {
+            if (r == c) {
+              trf += x;
+              frf += x * x;
+            } else {
+              frf += 2.0f * x * x;
+              // mirror (c, r): consecutive threads write consecutive r
+              const size_t m = (size_t)c * ld + r;
+              out0[m] = a;
+              out1[m] = b2;
+              if (fmt_bf16(F)) out2[m] = c2;
+              if (want_fp64) {
+                if (df) {
+                  out_hi[m] = x;
+                  out_lo[m] = 0.0f;
+                } else {
+                  out64[m] = (double)x;
+                }
+              }
+            }
+            if (want_fp64) {  // (r, c), a few products per solve: direct stores
+              const size_t d = (size_t)r * ld + c;
               if (df) {
-                out_hi[m] = x;
-                out_lo[m] = 0.0f;
+                out_hi[d] = x;
+                out_lo[d] = 0.0f;
               } else {
-                out64[m] = (double)x;
+                out64[d] = (double)x;
               }
             }
           }
@@ -339,41 +357,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       tr += (double)trf;
       fr += (double)frf;
-      // direct (r, c0..c0+31)
-      const size_t d = (size_t)r * ld + c0;
-      if (!diag) {
-        pack_store_row<F>(out, d, v0);
-        if (want_fp64) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (df) {
-              out_hi[d + j] = v0[j];
-              out_lo[d + j] = 0.0f;
-            } else {
-              out64[d + j] = (double)v0[j];
-            }
-          }
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (r <= c0 + j) {
-            uint16_t a, b2, c2;
-            split_value_f<F>(v0[j], a, b2, c2);
-            out[0][d + j] = a;
-            out[1][d + j] = b2;
-            if (fmt_bf16(F)) out[2][d + j] = c2;
-            if (want_fp64) {
-              if (df) {
-                out_hi[d + j] = v0[j];
-                out_lo[d + j] = 0.0f;
-              } else {
-                out64[d + j] = (double)v0[j];
-              }
-            }
-          }
+      // (r, c) slices: 32 rows of 32 columns back out, one row per store
+      __syncwarp();
+      const int cc = c0 + lane;
+#pragma unroll 4
+      for (int i = 0; i < 32; ++i) {
+        if (rb + i <= cc) {
+          const uint32_t v = stA[i * 33 + lane];
+          const size_t d = (size_t)(rb + i) * ld + cc;
+          out0[d] = (uint16_t)(v & 0xffffu);
+          out1[d] = (uint16_t)(v >> 16);
+          if (fmt_bf16(F)) out2[d] = stB[i * 34 + lane];
         }
       }
+      __syncwarp();
     }
   }
   tc_fence_before();

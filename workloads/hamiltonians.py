@@ -107,10 +107,10 @@ def batch_instance(index: int, sites: int, base_seed: int = 1000):
 
 def _fill_batch(args):
     """Worker: write instances [lo, hi) of a batch into a file-backed buffer."""
-    path, total, sites, offsets, lo, hi, base_seed = args
+    path, total, sites, offsets, lo, hi, base_seed, index = args
     buf = np.memmap(path, dtype=np.float64, mode="r+", shape=(total,))
     for i in range(lo, hi):
-        H, _ = cube_hamiltonian(int(sites[i]), base_seed + i)
+        H, _ = cube_hamiltonian(int(sites[i]), base_seed + int(index[i]))
         n = H.shape[0]
         buf[offsets[i]:offsets[i] + n * n] = H.ravel()
     buf.flush()
@@ -118,17 +118,21 @@ def _fill_batch(args):
     return hi - lo
 
 
-def batch_packed(sites, base_seed=1000, workers=None):
+def batch_packed(sites, base_seed=1000, workers=None, index=None):
     """All instances of a batch packed row-major into one FP64 vector.
 
-    Instance i is cube_hamiltonian(sites[i], base_seed + i); returns
-    (packed, n, offsets, nocc). Generation runs in `workers` processes
-    (spawned, so it is safe before or after CUDA initialisation) writing into
-    a temporary file-backed buffer."""
+    Instance i is cube_hamiltonian(sites[i], base_seed + index[i]) (index
+    defaults to 0, 1, ...: a rank's shard keeps the seeds of the whole
+    batch); returns (packed, n, offsets, nocc). Generation runs in `workers`
+    processes (spawned, so it is safe before or after CUDA initialisation)
+    writing into a temporary file-backed buffer."""
     import multiprocessing as mp
     import os
     import tempfile
     sites = np.asarray(sites, dtype=np.int64)
+    index = np.arange(len(sites)) if index is None else np.asarray(index, dtype=np.int64)
+    if len(index) != len(sites):
+        raise ValueError("index must have one entry per instance")
     n = (ORBITALS_PER_SITE * sites).astype(np.int32)
     sizes = n.astype(np.int64) ** 2
     offsets = np.zeros(len(n), dtype=np.int64)
@@ -142,7 +146,7 @@ def batch_packed(sites, base_seed=1000, workers=None):
     try:
         np.memmap(path, dtype=np.float64, mode="w+", shape=(max(total, 1),)).flush()
         chunks = np.linspace(0, len(n), max(1, workers * 4) + 1).astype(int)
-        jobs = [(path, total, sites, offsets, int(a), int(b), base_seed)
+        jobs = [(path, total, sites, offsets, int(a), int(b), base_seed, index)
                 for a, b in zip(chunks[:-1], chunks[1:]) if b > a]
         if workers > 1 and len(jobs) > 1:
             with mp.get_context("spawn").Pool(workers) as pool:
