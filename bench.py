@@ -432,9 +432,19 @@ def run_learned(args):
     M = torch.cat([lb["M"] for lb in labs])
     t_label = time.perf_counter() - t0
     P = L.Predictor(hidden=128, kmax=kmax, seed=0)
+    # hold out 10 % of the instances to calibrate the bound margin
+    perm = torch.randperm(X.shape[0], generator=torch.Generator().manual_seed(0)).to(X.device)
+    n_val = max(1, X.shape[0] // 10)
+    val, trn = perm[:n_val], perm[n_val:]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = P.fit(X, T, M, epochs=200, batch=512, lr=2e-3)
+    losses = P.fit(X[trn], T[trn], M[trn], epochs=200, batch=512, lr=2e-3)
+    # calibrate on the held-out instances closest in size to the evaluation
+    # set (the overshoot grows with n), all of them if too few
+    n_train = torch.from_numpy(4 * train_sites).to(X.device)
+    near = val[n_train[val] >= int(0.75 * 4 * args.eval_sites)]
+    cal = near if near.numel() >= 50 else val
+    margin = L.calibrate_margin(P.predict(X[cal]), T[cal])
     # stage 2: branch targets from runs with the predicted bounds
     T2s, M2s = [], []
     for lab, c0 in zip(labs, range(0, args.train_count, chunk)):
@@ -443,7 +453,9 @@ def run_learned(args):
         T2s.append(T2)
         M2s.append(M2)
         del b
-    losses += P.fit(X, torch.cat(T2s), torch.cat(M2s), epochs=200, batch=512, lr=1e-3)
+    T2, M2 = torch.cat(T2s), torch.cat(M2s)
+    losses += P.fit(X[trn], T2[trn], M2[trn], epochs=200, batch=512, lr=1e-3)
+    margin = L.calibrate_margin(P.predict(X[cal]), T[cal])
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     packed, n, offsets, nocc = batch_packed(np.full(args.eval_count, args.eval_sites), 50000)
@@ -476,7 +488,11 @@ def run_learned(args):
             "config": {"workload": f"learned bounds/branches: train {args.train_count} cube "
                                    f"instances (n 256..2048), eval {args.eval_count} x "
                                    f"n = {4 * args.eval_sites}",
-                       "hidden": 128, "kmax": kmax, "margin": margin, "judge_delta": 0.5,
+                       "hidden": 128, "kmax": kmax, "judge_delta": 0.5,
+                       "margin": margin, "margin_rule": "0.97 quantile of the bound overshoot "
+                                                        "on held-out training instances of "
+                                                        "n >= 0.75 n_eval (10 % held out)",
+                       "calibration_instances": int(cal.numel()),
                        "products": "per solve, a rejected predicted run included"},
             "plain": {"solves_per_s": args.eval_count / t_plain,
                       "products_mean": plain["products"].double().mean().item()},

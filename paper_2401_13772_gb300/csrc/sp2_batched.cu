@@ -515,24 +515,36 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll 1
             for (int ch = 0; ch < Cfg::COLS_PER_WARP / 32; ++ch) {
               const int cofs = half * Cfg::COLS_PER_WARP + ch * 32;  // column in the tile
-              float v0[32], v1[32];
-              tmem_ld32(tmem + lane_base + ACC_COLS * tb + cofs, v0);
-              if (NS == 2) tmem_ld32(tmem + lane_base + ACC_COLS * tb + BN + cofs, v1);
-              tmem_ld_wait();
               const int c0 = J * BN + cofs;
               float trf = 0.0f, frf = 0.0f;
 #pragma unroll
               for (int hh = 0; hh < 2; ++hh) {
+                // X at the mirror (for 2X - X^2) does not depend on the
+                // products: load it before the tensor-memory reads (packed
+                // slice0 | slice1 << 16; coalesced across the warp's rows)
+                uint32_t m01[16], m2[16];
+                if (bit) {
+#pragma unroll
+                  for (int jj = 0; jj < 16; ++jj) {
+                    const size_t mi = (size_t)(in.row0 + c0 + hh * 16 + jj) * P + r;
+                    m01[jj] = (uint32_t)xs0[mi] | ((uint32_t)xs1[mi] << 16);
+                    m2[jj] = NS == 3 ? (uint32_t)xs2[mi] : 0u;
+                  }
+                }
+                uint32_t u0[16], u1[16];
+                tmem_ld16(tmem + lane_base + ACC_COLS * tb + cofs + hh * 16, u0);
+                if (NS == 2) tmem_ld16(tmem + lane_base + ACC_COLS * tb + BN + cofs + hh * 16, u1);
+                tmem_ld_wait();
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {
-                  const int j = hh * 16 + jj;
-                  const int c = c0 + j;
-                  float x = (NS == 2) ? v0[j] + v1[j] * (1.0f / 2048.0f) : v0[j];
-                  if (bit) {
-                    const size_t mi = (size_t)(in.row0 + c) * P + r;
-                    x = 2.0f * join_value<F>(xs0[mi], xs1[mi], NS == 3 ? xs2[mi] : (uint16_t)0) -
+                  const int c = c0 + hh * 16 + jj;
+                  float x = (NS == 2)
+                                ? __uint_as_float(u0[jj]) + __uint_as_float(u1[jj]) * (1.0f / 2048.0f)
+                                : __uint_as_float(u0[jj]);
+                  if (bit)
+                    x = 2.0f * join_value<F>((uint16_t)(m01[jj] & 0xffffu),
+                                             (uint16_t)(m01[jj] >> 16), (uint16_t)m2[jj]) -
                         x;
-                  }
                   if (r <= c) {
                     uint16_t a, b, c2;
                     split_value_f<F>(x, a, b, c2);

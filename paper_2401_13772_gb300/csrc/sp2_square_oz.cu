@@ -30,8 +30,8 @@
 // is written back as double-float planes.
 //
 // Roles (one CTA per 128 x 128 upper-triangle tile, 384 threads):
-//   warp 0 lane 0 : TMA producer, 5 + 5 digit boxes of 128 x 32 (64 B rows,
-//                   64 B swizzle) per stage, two stages
+//   warp 0 lane 0 : TMA producer, 5 + 5 digit boxes of 128 x 16 (32 B rows,
+//                   32 B swizzle) per stage, five stages
 //   warp 1 lane 0 : MMA issuer (kind::f16 with BF16 operands, M = N = 128,
 //                   K = 16); per stage it issues the G2 products first, so
 //                   that at the end of a chunk the drain can read G2 while
@@ -54,32 +54,38 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128;
-constexpr int BK = 32;                       // 16-bit elements = 64 B rows
-constexpr int BOX_BYTES = BM * BK * 2;       // 8 KB
+constexpr int BK = 16;                       // 16-bit elements = 32 B rows
+constexpr int BOX_BYTES = BM * BK * 2;       // 4 KB
 constexpr int ND = 5;                        // digits
-constexpr int STAGES = 2;
-constexpr int STAGE_BYTES = 2 * ND * BOX_BYTES;  // 80 KB
-constexpr int CHUNK_KB = 4;                  // k-blocks per G2 chunk (128 k)
+constexpr int STAGES = 5;
+constexpr int STAGE_BYTES = 2 * ND * BOX_BYTES;  // 40 KB
+constexpr int CHUNK_KB = 128 / BK;           // k-blocks per G2 chunk (128 k)
 constexpr int THREADS = 384;
 constexpr int EPI_WARP0 = 4;
 constexpr int NEPI = 8;
 constexpr int TMEM_COLS = 512;               // G0 | G1 | G2 | T
 constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
 constexpr int kMaxOrder = 8192;              // G1 exactness bound
+// epilogue use of the (then idle) operand ring: staging of the (r, c) stores,
+// then the G2 sums of every epilogue thread
+constexpr int STAGING_BYTES = NEPI * 2 * 32 * 17 * 4;
+constexpr int G2S_OFFSET = 36864;
+static_assert(STAGING_BYTES <= G2S_OFFSET, "staging overlaps the G2 sums");
+static_assert(G2S_OFFSET + NEPI * 64 * 32 * 4 <= STAGES * STAGE_BYTES, "ring too small");
 
 struct OzMaps {
-  CUtensorMap d[ND];  // digit planes, 32 x 128 boxes
+  CUtensorMap d[ND];  // digit planes, 16 x 128 boxes
 };
 
-// Shared-memory matrix descriptor: K-major operand, 64 B swizzle (8-row atoms
-// of 512 B), sm_100-family version bit.
-__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major operand, 32 B swizzle (8-row atoms
+// of 256 B), sm_100-family version bit.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)(256 >> 4) << 32;   // stride byte offset: 8 rows x 32 B
   d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)4 << 61;            // SWIZZLE_64B
+  d |= (uint64_t)6 << 61;            // SWIZZLE_32B
   return d;
 }
 
@@ -137,20 +143,27 @@ __global__ void __launch_bounds__(256) digits_kernel(DevBuffers buf, int ld) {
     uint32_t w[ND][2];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const float hv = e == 0 ? h.x : (e == 1 ? h.y : (e == 2 ? h.z : h.w));
-      const float lv = e == 0 ? l.x : (e == 1 ? l.y : (e == 2 ? l.z : l.w));
-      // x rounded to 52 fractional bits (both products by 2^52 are exact)
-      long long v = __float2ll_rn(hv * 4503599627370496.0f) +
-                    __float2ll_rn(lv * 4503599627370496.0f);
+      // x = hi + lo; the remainder is carried as an unevaluated pair (rh, rl)
+      // renormalized by two-sum before each digit, so that every step is
+      // exact: a = rint(rh) is an integer of at most 9 bits and rh - a is
+      // exact (|rh - a| <= 1/2, Sterbenz), scalings are by powers of two.
+      float rh = (e == 0 ? h.x : (e == 1 ? h.y : (e == 2 ? h.z : h.w))) * 256.0f;
+      float rl = (e == 0 ? l.x : (e == 1 ? l.y : (e == 2 ? l.z : l.w))) * 256.0f;
 #pragma unroll
       for (int s = 0; s < ND; ++s) {
-        const int pos = 44 - 9 * s;
-        long long a = (v + (1ll << (pos - 1))) >> pos;  // nearest, ties up
-        if (s == 0) a = a > 256 ? 256 : (a < -256 ? -256 : a);  // |x| <= 1 in a valid run
-        v -= a << pos;
-        // a 2^(pos - 52) is exact in BF16: |a| <= 256
+        if (s > 0) {
+          rh *= 512.0f;
+          rl *= 512.0f;
+        }
+        float t;
+        two_sum(rh, rl, rh, t);
+        rl = t;
+        float a = rintf(rh);
+        if (s == 0) a = fminf(fmaxf(a, -256.0f), 256.0f);  // |x| <= 1 in a valid run
+        rh -= a;
+        // a 2^-(8 + 9 s) is exact in BF16: |a| <= 256
         const uint32_t bits = __bfloat16_as_ushort(
-            __float2bfloat16_rn((float)a * __int_as_float((127 + pos - 52) << 23)));
+            __float2bfloat16_rn(a * __int_as_float((127 - 8 - 9 * s) << 23)));
         if (e & 1)
           w[s][e >> 1] |= bits << 16;
         else
@@ -278,8 +291,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint64_t a[ND], b[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-          a[d] = smem_desc_sw64(sa + d * BOX_BYTES);
-          b[d] = same ? a[d] : smem_desc_sw64(sa + (ND + d) * BOX_BYTES);
+          a[d] = smem_desc_sw32(sa + d * BOX_BYTES);
+          b[d] = same ? a[d] : smem_desc_sw32(sa + (ND + d) * BOX_BYTES);
         }
         // G2 first
 #pragma unroll
@@ -361,21 +374,39 @@ __global__ void __launch_bounds__(THREADS, 1)
     // 32 rows x 16 columns of hi and of lo, row stride 17 floats
     float* stg = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw))) +
                  (warp - EPI_WARP0) * (2 * 32 * 17);
+    // the G2 sums move to shared memory (behind the staging area), freeing
+    // their registers for the epilogue: [warp][column][lane]
+    int* g2s = reinterpret_cast<int*>(smem_raw + (base - smem_u32(smem_raw)) + G2S_OFFSET) +
+               (warp - EPI_WARP0) * (64 * 32);
+#pragma unroll
+    for (int j = 0; j < 64; ++j) g2s[j * 32 + lane] = g2acc[j];
+    __syncwarp();
     float trh = 0.0f, trl = 0.0f, frh = 0.0f, frl = 0.0f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int col = half * 64 + q * 16;  // column in the tile
+      const int c0 = row_b + col;
+      // X at the mirror (for 2X - S) does not depend on the products: load
+      // it before the tensor-memory reads (X symmetric: coalesced)
+      float xmh[16], xml[16];
+      if (bit) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const size_t m = (size_t)(c0 + j) * ld + r;
+          xmh[j] = Xh[m];
+          xml[j] = Xl[m];
+        }
+      }
       uint32_t u0[16], u1[16], ut[16];
       tmem_ld16(lane_addr + col, u0);
       tmem_ld16(lane_addr + 128 + col, u1);
       tmem_ld16(lane_addr + 384 + col, ut);
       tmem_ld_wait();
-      const int c0 = row_b + col;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int c = c0 + j;
         // S = G0 + G1 + 2^-34 g2 + T in double-float
-        const int gi = g2acc[q * 16 + j];
+        const int gi = g2s[(q * 16 + j) * 32 + lane];
         const float g2h = (float)gi;
         const float g2l = (float)(gi - (int)g2h);  // exact remainder
         float s, e, e2;
@@ -386,10 +417,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         e += e2 + g2l * 5.820766091346741e-11f;
         float yh = s + e;
         float yl = e - (yh - s);
-        if (bit) {
-          const size_t m = (size_t)c * ld + r;  // X symmetric: the mirror is coalesced
-          dfz_sub(2.0f * Xh[m], 2.0f * Xl[m], yh, yl, yh, yl);
-        }
+        if (bit) dfz_sub(2.0f * xmh[j], 2.0f * xml[j], yh, yl, yh, yl);
         stg[lane * 17 + j] = yh;
         stg[32 * 17 + lane * 17 + j] = yl;
         if (r <= c) {
@@ -501,7 +529,7 @@ bool encode_oz_maps(const DevBuffers& b, int ld, OzMaps* maps) {
     cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
     cuuint32_t estr[2] = {1, 1};
     if (enc(&maps->d[d], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)b.dg[d], dims, strides, box,
-            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
   }

@@ -240,6 +240,19 @@ def predicted_bounds(Y, emin, emax, margin):
     return torch.stack([lo, hi], dim=1).contiguous()
 
 
+def calibrate_margin(Y, T, quantile=0.97, floor=0.02):
+    """Margin (fraction of the Gershgorin width) that covers the predicted
+    bounds' overshoot on held-out instances: the `quantile` of
+    max(y_j - t_j) over both bounds, never below `floor`. A run whose bounds
+    cut the spectrum is rejected by the judge and restarts on the plain path,
+    so the quantile sets the expected fallback rate of that cause."""
+    import torch
+    over = torch.clamp(Y[:, :2].double() - T[:, :2].double(), min=0.0).max(dim=1).values
+    if over.numel() == 0:
+        return float(floor)
+    return max(float(floor), float(torch.quantile(over, quantile).item()))
+
+
 def make_targets(u_min, u_max, bits, iters, kmax):
     """Targets and masks: the two bound fractions, then the branch bits of the
     labelled SP2 run (masked beyond its product count)."""
