@@ -175,10 +175,16 @@ progress_status_t progress_sp2_dense_noalloc(const double* dH, int64_t n, int64_
  * Batched SP2: `batch` independent dense problems of uneven size -- the parts
  * of a graph-partitioned system, which are independent and solved concurrently
  * (§VIII.B) -- in one persistent kernel launch (captured once in a CUDA graph
- * and replayed while the batch layout and pointers stay the same). Each CTA
- * takes whole instances, largest first, from a device work queue and runs
- * their full SP2 loop itself (split FP16 hi+lo products on tcgen05 tensor
- * cores, FP32 accumulation, FP64 traces and decisions).
+ * and replayed while the batch layout and pointers stay the same). Instances
+ * are taken largest first from a device work queue by thread-block clusters:
+ * a large instance by a whole cluster (its product tiles spread over the
+ * cluster's CTAs, traces exchanged through distributed shared memory), a
+ * small one by a single CTA, which runs its full SP2 loop (split FP16 hi+lo
+ * products on tcgen05 tensor cores, FP32 accumulation, FP64 traces and
+ * decisions). The tile shape, cluster size and sharing threshold are the
+ * ones progress_sp2_batched_tune chose for this batch signature, else
+ * 128 x 64 tiles, clusters of 2, sharing from 2 row blocks of 128; the _ex
+ * entry point can set them explicitly.
  *   h_n, h_offset, h_nocc  HOST arrays [batch]: order n_i (1..4096), element
  *                          offset of instance i in dH/dD, occupied states
  *   dH  device, packed FP64 inputs: instance i is n_i x n_i row-major at

@@ -24,8 +24,9 @@ using sp2::batched::InstanceInfo;
 using sp2::batched::Params;
 
 // Launch configuration used when neither the caller nor the autotuner chose
-// one: 128 x 128 tiles, clusters of two CTAs sharing parts of >= 3 row blocks.
-constexpr Config kDefaultConfig = {128, 2, 3, 0};
+// one: 128 x 64 tiles, clusters of two CTAs sharing parts of >= 2 row blocks
+// (among the fastest candidates on the 4000-part workload).
+constexpr Config kDefaultConfig = {64, 2, 2, 0};
 
 // Autotuned configurations by batch signature (device, slice format, pitch,
 // floor(log2(batch))).
