@@ -37,10 +37,14 @@ METRIC = "SP2 solves/s & tensor TFLOP/s vs plain FP64 SP2, same GB300, at stated
 UNIT = "solves/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 NOMINAL_BF16_TFLOPS = 2250.0
+OZ_KERNEL = ("square_oz_kernel (BF16 digit products, tcgen05; time includes digits_kernel, "
+             "traffic is square_oz_kernel's)")
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands, keyed by (kernel, n); see profiles/.
 NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200,
-               ("square_df64_kernel (double-float, FP32 pipe)", 4096): 521512448}
+               ("square_df64_kernel (double-float, FP32 pipe)", 4096): 521512448,
+               ("square_split_kernel (tcgen05)", 4096): 161894656,
+               (OZ_KERNEL, 4096): 658666752}
 NOMINAL_FP64_TFLOPS = 1.25
 DF_OPS = 12  # FP32 instructions per double-float multiply-add in square_df64_kernel
 OZ_PRODUCTS = 15  # BF16 digit products per FP64-accurate product in square_oz_kernel
@@ -648,8 +652,7 @@ def main():
         k64, p64, n64, b64 = ("square_df64_kernel (double-float, FP32 pipe)", df_peak, notedf,
                               "alu")
     elif impl == "digits":
-        k64, p64, b64 = ("square_oz_kernel + digits_kernel (BF16 digit products, tcgen05)",
-                         bf16_peak / OZ_PRODUCTS, "tensor")
+        k64, p64, b64 = (OZ_KERNEL, bf16_peak / OZ_PRODUCTS, "tensor")
         n64 = (f"fp16/bf16 dense, {peak_src} burst / {OZ_PRODUCTS} BF16 digit products per "
                f"FP64-accurate product")
     else:
