@@ -280,12 +280,6 @@ __global__ void __launch_bounds__(THREADS, 1)
           ok = false;
           break;
         }
-        if (chunk_first && c > 0) {  // the drain has read G2 of the previous chunk
-          if (!mbar_wait(g2empty, (uint32_t)(c - 1) & 1u, err)) {
-            ok = false;
-            break;
-          }
-        }
         tc_fence_after();
         const uint32_t sa = base + s * STAGE_BYTES;
         uint64_t a[ND], b[ND];
@@ -294,33 +288,54 @@ __global__ void __launch_bounds__(THREADS, 1)
           a[d] = smem_desc_sw32(sa + d * BOX_BYTES);
           b[d] = same ? a[d] : smem_desc_sw32(sa + (ND + d) * BOX_BYTES);
         }
-        // G2 first
+        // G0, G1 and T do not touch G2: at the first block of a chunk they
+        // go first, so that the drain of the previous chunk's G2 overlaps
+        // them; elsewhere G2 goes first, so that the last block's G2 commit
+        // is followed by that block's other products as well.
+        auto issue_rest = [&]() {
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 32 B per K = 16 step
-          const uint32_t c_acc = (chunk_first && kk == 0) ? 0u : 1u;
-          mma_f16(g2, a[0] + adv, b[2] + adv, idesc, c_acc);
-          mma_f16(g2, a[1] + adv, b[1] + adv, idesc, 1u);
-          mma_f16(g2, a[2] + adv, b[0] + adv, idesc, 1u);
-        }
-        if (chunk_last) mma_commit(g2full);
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 32 B per K = 16 step
+            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            mma_f16(g0, a[0] + adv, b[0] + adv, idesc, first);
+            mma_f16(g1, a[0] + adv, b[1] + adv, idesc, first);
+            mma_f16(g1, a[1] + adv, b[0] + adv, idesc, 1u);
+            // T: small terms first
+            mma_f16(tt, a[0] + adv, b[4] + adv, idesc, first);
+            mma_f16(tt, a[4] + adv, b[0] + adv, idesc, 1u);
+            mma_f16(tt, a[1] + adv, b[3] + adv, idesc, 1u);
+            mma_f16(tt, a[3] + adv, b[1] + adv, idesc, 1u);
+            mma_f16(tt, a[2] + adv, b[2] + adv, idesc, 1u);
+            mma_f16(tt, a[0] + adv, b[3] + adv, idesc, 1u);
+            mma_f16(tt, a[3] + adv, b[0] + adv, idesc, 1u);
+            mma_f16(tt, a[1] + adv, b[2] + adv, idesc, 1u);
+            mma_f16(tt, a[2] + adv, b[1] + adv, idesc, 1u);
+          }
+        };
+        auto issue_g2 = [&]() {
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-          const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-          mma_f16(g0, a[0] + adv, b[0] + adv, idesc, first);
-          mma_f16(g1, a[0] + adv, b[1] + adv, idesc, first);
-          mma_f16(g1, a[1] + adv, b[0] + adv, idesc, 1u);
-          // T: small terms first
-          mma_f16(tt, a[0] + adv, b[4] + adv, idesc, first);
-          mma_f16(tt, a[4] + adv, b[0] + adv, idesc, 1u);
-          mma_f16(tt, a[1] + adv, b[3] + adv, idesc, 1u);
-          mma_f16(tt, a[3] + adv, b[1] + adv, idesc, 1u);
-          mma_f16(tt, a[2] + adv, b[2] + adv, idesc, 1u);
-          mma_f16(tt, a[0] + adv, b[3] + adv, idesc, 1u);
-          mma_f16(tt, a[3] + adv, b[0] + adv, idesc, 1u);
-          mma_f16(tt, a[1] + adv, b[2] + adv, idesc, 1u);
-          mma_f16(tt, a[2] + adv, b[1] + adv, idesc, 1u);
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+            const uint32_t c_acc = (chunk_first && kk == 0) ? 0u : 1u;
+            mma_f16(g2, a[0] + adv, b[2] + adv, idesc, c_acc);
+            mma_f16(g2, a[1] + adv, b[1] + adv, idesc, 1u);
+            mma_f16(g2, a[2] + adv, b[0] + adv, idesc, 1u);
+          }
+          if (chunk_last) mma_commit(g2full);
+        };
+        if (chunk_first) {
+          issue_rest();
+          if (c > 0) {  // the drain has read G2 of the previous chunk
+            if (!mbar_wait(g2empty, (uint32_t)(c - 1) & 1u, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          issue_g2();
+        } else {
+          issue_g2();
+          issue_rest();
         }
         mma_commit(empty_bar(s));
         s_consumed = kb + 1;
@@ -342,18 +357,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int c = 0; c < NC; ++c) {
       if (!mbar_wait(g2full, (uint32_t)c & 1u, err)) break;
       tc_fence_after();
+      uint32_t v[64];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t v[16];
-        tmem_ld16(lane_addr + 256 + half * 64 + q * 16, v);
-        tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 16; ++j)  // exact: an integer number of 2^-34 below 2^24
-          g2acc[q * 16 + j] += __float2int_rn(__uint_as_float(v[j]) * 17179869184.0f);
-      }
+      for (int q = 0; q < 4; ++q) tmem_ld16(lane_addr + 256 + half * 64 + q * 16, v + q * 16);
+      tmem_ld_wait();
+      // the chunk is in registers: free G2 for the next chunk's products first
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(g2empty);
+#pragma unroll
+      for (int j = 0; j < 64; ++j)  // exact: an integer number of 2^-34 below 2^24
+        g2acc[j] += __float2int_rn(__uint_as_float(v[j]) * 17179869184.0f);
     }
   }
   const bool ok = mbar_wait(accum_bar, 0u, err, false);

@@ -14,8 +14,9 @@
 //                      weight group of the slices: acc0 += hi*hi^T,
 //                      acc1 += hi*lo^T + lo*hi^T (x2) or hi*mid^T + mid*hi^T
 //                      (x3), acc2 += hi*lo^T + lo*hi^T + mid*mid^T (x3).
-//                      The leading group acc0 alternates between two chunk
-//                      buffers of CHUNK k-blocks (K = 256): the tensor core's
+//                      The leading group acc0 rotates through three (x2) or
+//                      two (x3) chunk buffers of CHUNK k-blocks (K = 256), so
+//                      the MMA runs ahead of the drain: the tensor core's
 //                      FP32 accumulation truncates, and over a whole K = n
 //                      chain of same-sign products (the diagonal of X*X) that
 //                      truncation becomes a measurable bias; short chains
@@ -61,7 +62,7 @@ constexpr int DRAIN_WARPS = 8;     // two per 32-lane quarter of tensor memory
 constexpr int DRAIN_WARP0 = 4;
 constexpr int DCOLS = BN / 2;      // columns per drain thread
 constexpr int CHUNK = 4;           // k-blocks per leading-group accumulation chunk
-constexpr int TMEM_COLS = 512;     // acc0 x2 | acc1 | acc2, 128 columns each
+constexpr int TMEM_COLS = 512;     // acc0 chunk buffers | acc1 | (acc2), 128 columns each
 
 
 template <int F>
@@ -69,6 +70,9 @@ struct Cfg {
   static constexpr int NS = fmt_slices(F);                          // slices
   static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;            // A and B boxes
   static constexpr int STAGES = fmt_bf16(F) ? 2 : 3;
+  // leading-group chunk buffers in tensor memory: three for FP16x2 (acc1 in
+  // the fourth 128 columns), two for BF16x3 (acc1, acc2 in the others)
+  static constexpr int NBUF = fmt_bf16(F) ? 2 : 3;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;    // + align + barriers
 };
 
@@ -121,8 +125,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   auto empty_bar = [&](int s) { return bars + 8u * (C::STAGES + s); };
   const uint32_t accum_bar = bars + 8u * (2 * C::STAGES);
 
-  const uint32_t chunk_full = bars + 8u * (2 * C::STAGES + 1);   // [2]
-  const uint32_t chunk_empty = bars + 8u * (2 * C::STAGES + 3);  // [2]
+  const uint32_t chunk_full = bars + 8u * (2 * C::STAGES + 1);              // [NBUF]
+  const uint32_t chunk_empty = bars + 8u * (2 * C::STAGES + 1 + C::NBUF);   // [NBUF]
 
   if (threadIdx.x == 0) {
     s_err = 0;
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(empty_bar(s), 1);
     }
     mbar_init(accum_bar, 1);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < C::NBUF; ++b) {
       mbar_init(chunk_full + 8u * b, 1);
       mbar_init(chunk_empty + 8u * b, DRAIN_WARPS);
     }
@@ -173,15 +177,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       // (CHUNK k-blocks each) that the drain warps empty in turn; the
       // correction groups accumulate over the whole K.
       constexpr uint32_t idesc = idesc_f16(fmt_bf16(F) ? 1 : 0, BM, BN);
-      const uint32_t acc1 = tmem + 256, acc2 = tmem + 384;
+      const uint32_t acc1 = tmem + 128u * C::NBUF, acc2 = acc1 + 128u;
       bool ok = true;
       for (int kb = 0; kb < KB && ok; ++kb) {
-        const int c = kb / CHUNK, cb = c & 1;
+        const int c = kb / CHUNK, cb = c % C::NBUF;
         const bool chunk_first = (kb % CHUNK) == 0;
         const bool chunk_last = (kb % CHUNK) == CHUNK - 1 || kb == KB - 1;
         const uint32_t acc0 = tmem + 128u * cb;
         if (chunk_first) {
-          if (!mbar_wait(chunk_empty + 8u * cb, ((uint32_t)(c >> 1) & 1u) ^ 1u, err)) {
+          if (!mbar_wait(chunk_empty + 8u * cb, ((uint32_t)(c / C::NBUF) & 1u) ^ 1u, err)) {
             ok = false;
             break;
           }
@@ -237,22 +241,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   for (int j = 0; j < DCOLS; ++j) sum0[j] = 0.0f;
   if (drain) {
     for (int c = 0; c < NC; ++c) {
-      const int cb = c & 1;
-      if (!mbar_wait(chunk_full + 8u * cb, (uint32_t)(c >> 1) & 1u, err)) break;
+      const int cb = c % C::NBUF;
+      if (!mbar_wait(chunk_full + 8u * cb, (uint32_t)(c / C::NBUF) & 1u, err)) break;
       tc_fence_after();
+      float v[DCOLS];
 #pragma unroll
-      for (int q = 0; q < DCOLS / 32; ++q) {
-        float v[32];
-        tmem_ld32(lane_addr + 128u * cb + half * DCOLS + q * 32, v);
-        tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) sum0[q * 32 + j] += v[j];
-      }
+      for (int q = 0; q < DCOLS / 32; ++q) tmem_ld32(lane_addr + 128u * cb + half * DCOLS + q * 32, v + q * 32);
+      tmem_ld_wait();
+      // the values are in registers: free the buffer before adding them
       tc_fence_before();
       __syncwarp();
       if (lane == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(chunk_empty + 8u * cb)
                      : "memory");
+#pragma unroll
+      for (int j = 0; j < DCOLS; ++j) sum0[j] += v[j];
     }
   }
   // (the MMA thread always commits accum_bar, so this wait does not abort
@@ -306,8 +309,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
         uint32_t u1[16], u2[16];
-        tmem_ld16(lane_addr + 256 + col + hh * 16, u1);
-        if (fmt_bf16(F)) tmem_ld16(lane_addr + 384 + col + hh * 16, u2);
+        tmem_ld16(lane_addr + 128u * C::NBUF + col + hh * 16, u1);
+        if (fmt_bf16(F)) tmem_ld16(lane_addr + 128u * (C::NBUF + 1) + col + hh * 16, u2);
         tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
