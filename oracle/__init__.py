@@ -17,6 +17,9 @@ computes, written from the paper (arXiv 2401.13772):
   iteration count are fixed by the spectrum).
 * ``mlp`` -- forward/backward of the small MLP used by the learned-sequence
   path, written as plain numpy algebra, for gradient checks.
+* ``graph`` -- the graph-based divide-and-conquer density matrix of §VIII.B
+  (threshold graph, core and core-halo partitions, submatrices, SP2 at a
+  fixed chemical potential, core columns mapped back).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 leg may import this package. It shares no code with the CUDA path and the
@@ -35,3 +38,10 @@ from .sp2 import (  # noqa: F401
     PAPER,
 )
 from .eig import jacobi_eigh, build_oracle  # noqa: F401
+from .graph import (  # noqa: F401
+    threshold_graph,
+    core_partition,
+    core_halo,
+    sp2_fixed_mu,
+    graph_density,
+)
