@@ -86,10 +86,14 @@ def parse_args():
                     help="skip the torch-side invariants of D (profiling runs)")
     ap.add_argument("--loop-mode", type=int, default=0,
                     help="0: device-driven WHILE graph; 1: plain launches (profilers)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "learned"],
+    ap.add_argument("--workload", default="dense",
+                    choices=["dense", "batched", "learned", "graph"],
                     help="dense: one N = 4096 cube solve per step (headline); batched: 4000 "
                          "parts of 64..768 orbitals per step; learned: predictor training "
-                         "and evaluation")
+                         "and evaluation; graph: graph-based divide and conquer of a chain")
+    ap.add_argument("--graph-n", type=int, default=8192)
+    ap.add_argument("--graph-tau", type=float, default=1e-5)
+    ap.add_argument("--graph-parts", type=int, default=16)
     ap.add_argument("--batch", type=int, default=4000)
     ap.add_argument("--batch-prec", default="fp32_split",
                     choices=["fp32_split", "fp32_split_bf16"])
@@ -537,6 +541,103 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_graph(args):
+    """Graph-based divide-and-conquer workload (§VIII.B): a gapped dimerized
+    chain of `--graph-n` orbitals at its mid-gap chemical potential; the
+    auxiliary matrix is a previously computed density matrix (here the dense
+    mixed solve of the same H, which is also the reference); `--graph-parts`
+    regular-segment cores, threshold `--graph-tau`. One step = one whole-system
+    density matrix from the core-halo parts (one batched SP2 launch)."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2401_13772_gb300 as pkg
+    from paper_2401_13772_gb300.build import build
+    from workloads import chain_hamiltonian
+    build()
+    dev = torch.device("cuda", 0)
+    H_np, nocc = chain_hamiltonian(args.graph_n, -1.0, -0.6)
+    n = H_np.shape[0]
+    H = torch.from_numpy(H_np).to(dev)
+    # reference and auxiliary matrix: the dense mixed solve (not timed)
+    Dref, dinfo = pkg.sp2_dense_ex(H, nocc, 1e-10, prec="mixed_fp16", fp64_prefix=8)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    pkg.sp2_dense_ex(H, nocc, 1e-10, D=torch.empty_like(H), prec="mixed_fp16", fp64_prefix=8,
+                     info=False)
+    e1.record()
+    torch.cuda.synchronize()
+    dense_ms = e0.elapsed_time(e1)
+    G = Dref.clone()
+    D = torch.empty_like(H)
+    tau, parts = args.graph_tau, args.graph_parts
+    for _ in range(max(1, args.warmup)):
+        D, ginfo = pkg.sp2_graph(H, G, tau, parts, 0.0, 1e-10, D=D)
+    torch.cuda.synchronize()
+    K = args.steps
+    clocks = ClockSampler()
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+    for i in range(K):
+        ev[2 * i].record()
+        pkg.sp2_graph(H, G, tau, parts, 0.0, 1e-10, D=D)
+        ev[2 * i + 1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(K)) / K / 1e3
+    Dn = D.cpu().numpy()
+    Dr = Dref.cpu().numpy()
+    err = float(np.abs(Dn - Dr).max())
+    # the oracle's graph solve on the host cores (same tau, parts, auxiliary)
+    t0 = time.perf_counter()
+    P, _ = oracle.graph_density(H_np, Dr, tau, parts, 0.0, 1e-10)
+    cpu_sec = time.perf_counter() - t0
+    err_oracle = float(np.abs(Dn - P).max())
+    # end to end: H and G in from pinned host memory, D out
+    Hh = torch.from_numpy(H_np).pin_memory()
+    Gh = G.cpu().pin_memory()
+    Dh = torch.empty_like(Hh).pin_memory()
+    torch.cuda.synchronize()
+    e0.record()
+    H.copy_(Hh, non_blocking=True)
+    G.copy_(Gh, non_blocking=True)
+    pkg.sp2_graph(H, G, tau, parts, 0.0, 1e-10, D=D)
+    Dh.copy_(D, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_sec = e0.elapsed_time(e1) / 1e3
+    s_mean = ginfo["mean_part"]
+    flops = ginfo["max_iters"] * parts * s_mean ** 3  # upper estimate of the SP2 products
+    peaks, src = load_peaks()
+    line = {"metric": METRIC, "value": 1.0 / sec, "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16x2 split, f32 accumulate",
+            "data": "synthetic",
+            "config": {"workload": f"graph-based divide and conquer: dimerized chain N={n} "
+                                   f"(t1=-1.0, t2=-0.6, gap 0.8), mu=0, {parts} regular-segment "
+                                   f"cores, tau={tau} on a previous density matrix",
+                       "parallelism": "one GPU"},
+            "parts": ginfo, "d_check": {"max_abs_err_vs_dense_solve": err,
+                                        "max_abs_err_vs_oracle_graph_solve": err_oracle},
+            "dense_mixed_solve_ms": dense_ms, "speedup_vs_dense": dense_ms / (sec * 1e3),
+            "roofline": {"bound": "tensor", "achieved": flops / sec / 1e12,
+                         "peak": peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]),
+                         "unit": "TFLOP/s", "traffic": None,
+                         "kernel": "batched_kernel (whole graph step timed)",
+                         "peak_source": f"fp16/bf16 dense, {src} burst",
+                         "flops_per_launch": flops},
+            "cpu_baseline": {"value": 1.0 / cpu_sec, "unit": UNIT, "cores": cpu_cores(),
+                             "kind": "oracle", "sample": "one whole graph solve (same tau, "
+                                                         "parts and auxiliary matrix)"},
+            "e2e": {"value": 1.0 / e2e_sec, "unit": UNIT,
+                    "h2d_bytes_per_step": int(2 * H_np.nbytes),
+                    "d2h_bytes_per_step": int(H_np.nbytes)},
+            "gpu_launches": 5 * K, "clocks": clk}
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -547,6 +648,9 @@ def main():
         return
     if args.workload == "learned":
         run_learned(args)
+        return
+    if args.workload == "graph":
+        run_graph(args)
         return
     import numpy as np
     import torch

@@ -70,7 +70,12 @@ typedef enum {
 typedef enum {
   PROGRESS_RULE_NEARER = 0, /* take the branch whose trace lands nearer Nocc; needs no extra
                                work because Tr X^2 = ||X||_F^2 is known before the product */
-  PROGRESS_RULE_PAPER = 1   /* 2X - X^2 iff Tr X - Nocc <= 0 (Listing 1's test) */
+  PROGRESS_RULE_PAPER = 1,  /* 2X - X^2 iff Tr X - Nocc <= 0 (Listing 1's test) */
+  PROGRESS_RULE_MU = 2      /* batched and graph solves only: D = theta(mu I - H) at a given
+                               chemical potential mu instead of a given Nocc. The X0 map sends
+                               mu to y = (emax - mu) / (emax - emin) (bounds widened to
+                               mu -/+ 1 if they do not hold mu strictly inside); each product
+                               is X^2 if y > 1/2, else 2X - X^2, and y follows the same map */
 } progress_rule_t;
 
 typedef struct {
@@ -226,6 +231,9 @@ typedef struct {
   int32_t reserved0;           /* must be zero */
   int64_t* d_cycles;           /* device [batch]: SM clock cycles spent on each instance (by
                                   the CTA that owns it, or cluster rank 0), or NULL */
+  const double* d_mu;          /* device [batch]: chemical potential of each instance; needed
+                                  with opts->rule = PROGRESS_RULE_MU (h_nocc is then ignored),
+                                  else NULL */
 } progress_batch_ex_t;
 
 /*
@@ -275,6 +283,39 @@ progress_status_t progress_sp2_batched_tune(int32_t batch, const int32_t* h_n,
                                             const progress_opts_t* opts, int32_t sample_stride,
                                             int32_t reps, progress_batch_tune_t* out,
                                             void* stream);
+
+/*
+ * Graph-based divide-and-conquer density matrix (§VIII.B): P ~ theta(mu I - H)
+ * for a large H from small dense parts.
+ *   1. adjacency of the auxiliary matrix G (H itself, an overlap matrix, or a
+ *      previously computed density matrix): A_ij = |G_ij| >= tau, i != j;
+ *   2. core partition: nparts regular segments of the index list (part k
+ *      holds [floor(k n / nparts), floor((k + 1) n / nparts)));
+ *   3. core-halo parts: each core plus every node adjacent to it;
+ *   4. the dense submatrices H[part, part], solved together in one batched
+ *      SP2 launch at the chemical potential mu (PROGRESS_RULE_MU; precision
+ *      from opts->prec, FP32_SPLIT or FP32_SPLIT_BF16; NULL = FP32_SPLIT);
+ *   5. the columns of each core copied into P, then P = (P + P^T) / 2.
+ *   dH, dG  device n x n row-major FP64 (read only); dD device n x n output
+ *   (must not overlap dH or dG). A part may hold at most 4096 nodes
+ *   (PROGRESS_EUNSUPPORTED otherwise). info (host, may be NULL): part
+ *   statistics. Synchronizes the stream (the part layout is built on the
+ *   host from the adjacency rows). The part buffers are cached per (device,
+ *   stream) like the other work spaces.
+ */
+typedef struct {
+  int32_t nparts;       /* parts solved */
+  int32_t max_part;     /* largest core-halo part (nodes) */
+  double mean_part;     /* mean core-halo part size */
+  int32_t max_iters;    /* most SP2 products of a part */
+  int32_t failed_parts; /* parts whose SP2 status was not PROGRESS_OK */
+  int64_t sub_elements; /* elements of all dense submatrices */
+} progress_graph_info_t;
+
+progress_status_t progress_sp2_graph(const double* dH, const double* dG, int64_t n, double tau,
+                                     int32_t nparts, double mu, double tol, double* dD,
+                                     const progress_opts_t* opts, progress_graph_info_t* info,
+                                     void* stream);
 
 /*
  * Features of the learned predictor, 37 floats per instance (device output
@@ -338,10 +379,11 @@ progress_status_t progress_sp2_query(void* stream, progress_info_t* info);
  */
 int32_t progress_sp2_history(void* stream, double* idem, double* margin, int32_t cap);
 
-/* Free the cached workspace of `stream` on the current device (synchronizes it). */
+/* Free the cached work spaces (dense, batched and graph solves) of `stream` on the
+ * current device (synchronizes it). */
 progress_status_t progress_release(void* stream);
 
-/* Free every cached workspace of the current device (synchronizes the device). */
+/* Free every cached work space of the current device (synchronizes the device). */
 progress_status_t progress_release_all(void);
 
 /* Text of the last error recorded by this thread (never NULL). */

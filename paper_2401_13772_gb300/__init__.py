@@ -19,6 +19,7 @@ import math
 from . import _lib
 from ._lib import (  # noqa: F401
     FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16, FP32_SPLIT_BF16, DF64, RULE_NEARER, RULE_PAPER,
+    RULE_MU,
     Info, Opts, ProgressError, load, check,
 )
 
@@ -28,7 +29,7 @@ __all__ = ["gershgorin_bounds", "sp2_dense", "sp2_dense_ex", "release", "load",
 
 PREC_NAMES = {"fp64": FP64, "fp32_split": FP32_SPLIT, "mixed_fp16": MIXED_FP16,
               "mixed_bf16": MIXED_BF16, "fp32_split_bf16": FP32_SPLIT_BF16, "df64": DF64}
-RULE_NAMES = {"nearer": RULE_NEARER, "paper": RULE_PAPER}
+RULE_NAMES = {"nearer": RULE_NEARER, "paper": RULE_PAPER, "mu": RULE_MU}
 
 
 def _stream_ptr(stream=None):
@@ -149,7 +150,7 @@ def _check_packed(H_packed):
 
 
 def sp2_batched(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", maxiter=100,
-                stream=None, prec="fp32_split", config=None, cycles=False):
+                stream=None, prec="fp32_split", config=None, cycles=False, mu=None):
     """Batched split-precision SP2 over packed device inputs.
 
     H_packed: 1-D float64 CUDA tensor; n, offsets, nocc: host int sequences.
@@ -157,7 +158,10 @@ def sp2_batched(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", m
     the library default) or (tile_n, cluster, share).
     Returns (D_packed, iters, status) with iters/status as int32 CUDA tensors,
     plus a per-instance int64 tensor of SM clock cycles when cycles=True.
+    mu: per-instance chemical potentials -> D_i = theta(mu_i I - H_i) (the
+    fixed-mu rule; nocc is then ignored).
     """
+    import numpy as np
     import torch
     _check_packed(H_packed)
     n, offsets, nocc = _batch_arrays(n, offsets, nocc)
@@ -166,6 +170,10 @@ def sp2_batched(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", m
         D_packed = torch.empty_like(H_packed)
     iters = torch.zeros(b, dtype=torch.int32, device=H_packed.device)
     status = torch.zeros(b, dtype=torch.int32, device=H_packed.device)
+    mu_d = None
+    if mu is not None:
+        rule = "mu"
+        mu_d = torch.as_tensor(np.asarray(mu, dtype=np.float64), device=H_packed.device)
     o = make_opts(prec=prec, rule=rule, maxiter=maxiter)
     cyc = None
     with torch.cuda.device(H_packed.device):
@@ -174,10 +182,12 @@ def sp2_batched(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", m
                 float(tol), ctypes.c_void_p(D_packed.data_ptr()),
                 ctypes.c_void_p(iters.data_ptr()), ctypes.c_void_p(status.data_ptr()),
                 ctypes.byref(o))
-        if config is None and not cycles:
+        if config is None and not cycles and mu_d is None:
             check(load().progress_sp2_batched(*args, _stream_ptr(stream)))
         else:
             ex = _lib.BatchEx()
+            if mu_d is not None:
+                ex.d_mu = mu_d.data_ptr()
             if config is not None:
                 ex.tile_n, ex.cluster, ex.share = (int(v) for v in config)
             if cycles:
@@ -209,6 +219,30 @@ def batched_tune(H_packed, n, offsets, nocc, tol, D_packed=None, rule="nearer", 
             ctypes.c_void_p(D_packed.data_ptr()), ctypes.byref(o), int(sample_stride), int(reps),
             ctypes.byref(out), _stream_ptr(stream)))
     return out.to_dict()
+
+
+def sp2_graph(H, G, tau, nparts, mu, tol, D=None, prec="fp32_split", maxiter=100, stream=None):
+    """Graph-based divide-and-conquer density matrix theta(mu I - H) (§VIII.B):
+    adjacency |G_ij| >= tau of the auxiliary matrix G, nparts regular-segment
+    cores extended by their neighbours, the dense parts solved in one batched
+    SP2 launch at the chemical potential mu, core columns mapped back.
+    H, G: square float64 CUDA tensors. Returns (D, info dict)."""
+    import torch
+    for M in (H, G):
+        if not (isinstance(M, torch.Tensor) and M.is_cuda and M.dtype == torch.float64 and
+                M.dim() == 2 and M.shape[0] == M.shape[1] and M.is_contiguous()):
+            raise TypeError("H and G must be square contiguous float64 CUDA tensors")
+    n = H.shape[0]
+    if D is None:
+        D = torch.empty_like(H)
+    o = make_opts(prec=prec, maxiter=maxiter)
+    info = _lib.GraphInfo()
+    with torch.cuda.device(H.device):
+        check(load().progress_sp2_graph(
+            ctypes.c_void_p(H.data_ptr()), ctypes.c_void_p(G.data_ptr()), n, float(tau),
+            int(nparts), float(mu), float(tol), ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
+            ctypes.byref(info), _stream_ptr(stream)))
+    return D, info.to_dict()
 
 
 def history(stream=None, cap=256):

@@ -18,7 +18,7 @@ STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOCONV: "ENOCONV", EBOUNDS: "EBOUND
                 EUNSUPPORTED: "EUNSUPPORTED"}
 
 FP64, FP32_SPLIT, MIXED_FP16, MIXED_BF16, FP32_SPLIT_BF16, DF64 = range(6)
-RULE_NEARER, RULE_PAPER = 0, 1
+RULE_NEARER, RULE_PAPER, RULE_MU = 0, 1, 2
 
 
 class Opts(ctypes.Structure):
@@ -53,7 +53,18 @@ class BatchEx(ctypes.Structure):
                 ("d_fallback", ctypes.c_void_p), ("d_products", ctypes.c_void_p),
                 ("tile_n", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("share", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("d_cycles", ctypes.c_void_p)]
+                ("d_cycles", ctypes.c_void_p), ("d_mu", ctypes.c_void_p)]
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("nparts", ctypes.c_int32), ("max_part", ctypes.c_int32),
+                ("mean_part", ctypes.c_double), ("max_iters", ctypes.c_int32),
+                ("failed_parts", ctypes.c_int32), ("sub_elements", ctypes.c_int64)]
+
+    def to_dict(self):
+        return {"nparts": self.nparts, "max_part": self.max_part, "mean_part": self.mean_part,
+                "max_iters": self.max_iters, "failed_parts": self.failed_parts,
+                "sub_elements": self.sub_elements}
 
 
 class BatchTune(ctypes.Structure):
@@ -86,6 +97,8 @@ SIGNATURES = {
     "progress_sp2_batched_tune": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _D, _P,
                                                  ctypes.POINTER(Opts), ctypes.c_int32,
                                                  ctypes.c_int32, ctypes.POINTER(BatchTune), _P]),
+    "progress_sp2_graph": (ctypes.c_int, [_P, _P, _I64, _D, ctypes.c_int32, _D, _D, _P,
+                                          ctypes.POINTER(Opts), ctypes.POINTER(GraphInfo), _P]),
     "progress_features": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P]),
     "progress_trace_hd": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
     "progress_mlp_param_count": (ctypes.c_int32, [ctypes.c_int32] * 3),

@@ -454,6 +454,9 @@ int32_t progress_sp2_history(void* stream, double* idem, double* margin, int32_t
 progress_status_t progress_release(void* stream) {
   int dev = 0;
   CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+  sp2::batched_release(dev, (cudaStream_t)stream, false);
+  sp2::graph_release(dev, (cudaStream_t)stream, false);
   Workspace* w = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -471,6 +474,8 @@ progress_status_t progress_release_all(void) {
   int dev = 0;
   CK(cudaGetDevice(&dev), "cudaGetDevice");
   CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  sp2::batched_release(dev, nullptr, true);
+  sp2::graph_release(dev, nullptr, true);
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto it = g_ws.begin(); it != g_ws.end();) {
     if (it->first.first == dev) {

@@ -364,6 +364,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         st.pred_len = min(prm.pred_len[inst], kMaxHist);
         st.judge_delta = prm.judge_delta;
       }
+      if (prm.rule == PROGRESS_RULE_MU) {
+        // theta(mu I - H): mu must map strictly inside (0, 1)
+        const double mu = prm.mu_in[inst];
+        if (!(st.emin < mu && mu < st.emax)) {
+          st.emin = fmin(st.emin, mu - 1.0);
+          st.emax = fmax(st.emax, mu + 1.0);
+        }
+        st.y_mu = (st.emax - mu) / (st.emax - st.emin);
+      }
       st.best_split_idem = INFINITY;
       st.phase = kPhaseSplit;
     }

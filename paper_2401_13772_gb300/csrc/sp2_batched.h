@@ -63,6 +63,7 @@ struct Params {
   int32_t* status;        // [batch] progress_status_t per instance (may be null)
   InstanceInfo* info;     // [batch] optional details
   long long* cycles;      // [batch] SM clock cycles the instance took (may be null)
+  const double* mu_in;    // [batch] chemical potentials (rule PROGRESS_RULE_MU)
 };
 
 // Valid configuration? (tile_n 64/128, cluster 1/2/4/8, share >= 1)

@@ -168,8 +168,11 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
                  "the batched solver runs PROGRESS_FP32_SPLIT or PROGRESS_FP32_SPLIT_BF16 only");
   const int fmt = o.prec == PROGRESS_FP32_SPLIT_BF16 ? sp2::kBF16x3 : sp2::kFP16x2;
   const int nsl = sp2::fmt_slices(fmt);
-  if (o.rule != PROGRESS_RULE_NEARER && o.rule != PROGRESS_RULE_PAPER)
+  const bool by_mu = o.rule == PROGRESS_RULE_MU;
+  if (o.rule != PROGRESS_RULE_NEARER && o.rule != PROGRESS_RULE_PAPER && !by_mu)
     return bfail(PROGRESS_EINVAL, "unknown branch rule");
+  if (by_mu && !(ex && ex->d_mu))
+    return bfail(PROGRESS_EINVAL, "PROGRESS_RULE_MU needs progress_batch_ex_t.d_mu");
   if (o.maxiter < 0 || o.maxiter > 250) return bfail(PROGRESS_EINVAL, "maxiter must be in [0, 250]");
   std::vector<Instance> inst(batch);
   int pitch = 0;
@@ -177,13 +180,14 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
   for (int i = 0; i < batch; ++i) {
     const int n = h_n[i];
     if (n < 1 || n > 4096) return bfail(PROGRESS_EINVAL, "every n_i must be in [1, 4096]");
-    if (h_nocc[i] < 0 || h_nocc[i] > n) return bfail(PROGRESS_EINVAL, "nocc_i must be in [0, n_i]");
+    if (!by_mu && (h_nocc[i] < 0 || h_nocc[i] > n))
+      return bfail(PROGRESS_EINVAL, "nocc_i must be in [0, n_i]");
     if (h_offset[i] < 0) return bfail(PROGRESS_EINVAL, "offsets must be >= 0");
     Instance& t = inst[i];
     memset(&t, 0, sizeof t);
     t.n = n;
     t.m = (n + 127) / 128 * 128;
-    t.nocc = h_nocc[i];
+    t.nocc = by_mu ? 0 : h_nocc[i];
     t.row0 = rows;
     t.offset = h_offset[i];
     rows += t.m;
@@ -297,6 +301,7 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
     prm.fallback = ex->d_fallback;
     prm.products = ex->d_products;
     prm.cycles = reinterpret_cast<long long*>(ex->d_cycles);
+    prm.mu_in = ex->d_mu;
   }
   prm.share = cfg.share;
 
@@ -454,3 +459,22 @@ extern "C" progress_status_t progress_sp2_batched_tune(
   if (out) *out = res;
   return PROGRESS_OK;
 }
+
+namespace sp2 {
+void batched_release(int dev, cudaStream_t s, bool all_streams) {
+  std::lock_guard<std::mutex> lk(g_bmu);
+  for (auto it = g_bws.begin(); it != g_bws.end();) {
+    if (it->first.first == dev && (all_streams || it->first.second == s)) {
+      BatchWs* w = it->second;
+      drop_graph(w);
+      free_bufs(w);
+      free_meta(w);
+      if (w->cap) cudaStreamDestroy(w->cap);
+      delete w;
+      it = g_bws.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+}  // namespace sp2

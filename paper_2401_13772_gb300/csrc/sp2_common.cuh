@@ -55,6 +55,7 @@ struct State {
   int pred_len;
   int judge_fail;
   double judge_delta;
+  double y_mu;  // PROGRESS_RULE_MU: the chemical potential under the same map as X_k
   unsigned long long bits[4];
   double idem_hist[kMaxHist];
   double margin_hist[kMaxHist];
@@ -195,7 +196,11 @@ __device__ inline void decide(State* st) {
   const double nocc = (double)st->nocc;
   int b;
   double margin;
-  if (st->rule == PROGRESS_RULE_PAPER) {
+  if (st->rule == PROGRESS_RULE_MU) {
+    // fixed chemical potential: the branch keeps the mapped mu near 1/2
+    margin = 0.5 - st->y_mu;
+    b = st->y_mu > 0.5 ? 0 : 1;
+  } else if (st->rule == PROGRESS_RULE_PAPER) {
     margin = nocc - t1;
     b = (t1 - nocc) <= 0.0 ? 1 : 0;
   } else {
@@ -220,6 +225,10 @@ __device__ inline void decide(State* st) {
     }
   }
   st->bit = b;
+  if (st->rule == PROGRESS_RULE_MU) {  // the mapped mu follows the branch taken
+    const double y = st->y_mu;
+    st->y_mu = b ? 2.0 * y - y * y : y * y;
+  }
   if (k < kMaxHist) {
     st->margin_hist[k] = margin;
     if (b) st->bits[k >> 6] |= 1ull << (k & 63);

@@ -52,9 +52,12 @@ def test_struct_sizes_match_header_layout():
     # progress_info_t: 6 int32, 4 double, 4 uint64
     assert ctypes.sizeof(_lib.Info) == 6 * 4 + 4 * 8 + 4 * 8
     assert _lib.Info.emin.offset == 24 and _lib.Info.bits.offset == 56
-    # progress_batch_ex_t: 8 pointer/double slots, 4 int32 (configuration), 1 pointer
-    assert ctypes.sizeof(_lib.BatchEx) == 8 * 8 + 4 * 4 + 8
+    # progress_batch_ex_t: 8 pointer/double slots, 4 int32 (configuration), 2 pointers
+    assert ctypes.sizeof(_lib.BatchEx) == 8 * 8 + 4 * 4 + 2 * 8
     assert _lib.BatchEx.tile_n.offset == 64 and _lib.BatchEx.d_cycles.offset == 80
+    assert _lib.BatchEx.d_mu.offset == 88
+    # progress_graph_info_t
+    assert ctypes.sizeof(_lib.GraphInfo) == 2 * 4 + 8 + 2 * 4 + 8
     # progress_batch_tune_t: 4 int32, int32 cand[16][3], float ms[16]
     assert ctypes.sizeof(_lib.BatchTune) == 4 * 4 + 16 * 3 * 4 + 16 * 4
     assert _lib.BatchTune.ms.offset == 16 + 16 * 3 * 4
@@ -74,6 +77,22 @@ def test_batched_argument_errors(lib):
                                          ctypes.byref(tune), None) == _lib.EINVAL
     assert lib.progress_sp2_batched_tune(2, n, off, nocc, P(16), 1e-9, P(32), None, 1, 3,
                                          ctypes.byref(tune), None) == _lib.EINVAL
+    # the fixed-mu rule needs the per-instance chemical potentials
+    o = _lib.Opts()
+    lib.progress_opts_default(ctypes.byref(o))
+    o.prec, o.rule = _lib.FP32_SPLIT, _lib.RULE_MU
+    n[1] = 64
+    assert lib.progress_sp2_batched(2, n, off, nocc, P(16), 1e-9, P(32), None, None,
+                                    ctypes.byref(o), None) == _lib.EINVAL
+    assert b"d_mu" in lib.progress_last_error()
+    # graph solver argument checks
+    gi = _lib.GraphInfo()
+    assert lib.progress_sp2_graph(P(16), P(16), 100, 1e-3, 0, 0.0, 1e-9, P(32), None,
+                                  ctypes.byref(gi), None) == _lib.EINVAL
+    assert lib.progress_sp2_graph(P(16), P(16), 100, -1.0, 4, 0.0, 1e-9, P(32), None,
+                                  ctypes.byref(gi), None) == _lib.EINVAL
+    assert lib.progress_sp2_graph(P(16), P(16), 100, 1e-3, 4, 0.0, 1e-9, P(16), None,
+                                  ctypes.byref(gi), None) == _lib.EINVAL
 
 
 def test_defaults_and_version(lib):
