@@ -187,9 +187,10 @@ progress_status_t progress_sp2_dense_noalloc(const double* dH, int64_t n, int64_
  * small one by a single CTA, which runs its full SP2 loop (split FP16 hi+lo
  * products on tcgen05 tensor cores, FP32 accumulation, FP64 traces and
  * decisions). The tile shape, cluster size and sharing threshold are the
- * ones progress_sp2_batched_tune chose for this batch signature, else
- * 128 x 64 tiles, clusters of 2, sharing from 2 row blocks of 128; the _ex
- * entry point can set them explicitly.
+ * ones progress_sp2_batched_tune chose for this batch signature, else a
+ * default (largest part below 1024: 128 x 64 tiles, clusters of 2, sharing
+ * from 2 row blocks of 128; otherwise 128 x 128 tiles, clusters of 2, sharing
+ * from 3 row blocks); the _ex entry point can set them explicitly.
  *   h_n, h_offset, h_nocc  HOST arrays [batch]: order n_i (1..4096), element
  *                          offset of instance i in dH/dD, occupied states
  *   dH  device, packed FP64 inputs: instance i is n_i x n_i row-major at

@@ -24,9 +24,12 @@ using sp2::batched::InstanceInfo;
 using sp2::batched::Params;
 
 // Launch configuration used when neither the caller nor the autotuner chose
-// one: 128 x 64 tiles, clusters of two CTAs sharing parts of >= 2 row blocks
-// (among the fastest candidates on the 4000-part workload).
-constexpr Config kDefaultConfig = {64, 2, 2, 0};
+// one: for parts of up to 768 orbitals 128 x 64 tiles, clusters of two CTAs
+// sharing parts of >= 2 row blocks (among the fastest candidates on 4000
+// parts of 64..768); for larger parts 128 x 128 tiles, clusters of two
+// sharing from 3 row blocks (1000 parts of 2048: 290 vs 207 solves/s).
+constexpr Config kDefaultSmall = {64, 2, 2, 0};
+constexpr Config kDefaultLarge = {128, 2, 3, 0};
 
 // Autotuned configurations by batch signature (device, slice format, pitch,
 // floor(log2(batch))).
@@ -200,7 +203,7 @@ progress_status_t batched_impl(int32_t batch, const int32_t* h_n, const int64_t*
   if (major != 10) return bfail(PROGRESS_EUNSUPPORTED, "the batched solver needs an sm_10x GPU");
   cudaStream_t s = (cudaStream_t)stream;
   // launch configuration: forced (autotuner), explicit (caller), tuned, default
-  Config cfg = kDefaultConfig;
+  Config cfg = pitch >= 1024 ? kDefaultLarge : kDefaultSmall;
   if (force) {
     cfg = *force;
   } else if (ex && (ex->tile_n || ex->cluster || ex->share)) {
