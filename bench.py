@@ -94,6 +94,9 @@ def parse_args():
     ap.add_argument("--graph-n", type=int, default=8192)
     ap.add_argument("--graph-tau", type=float, default=1e-5)
     ap.add_argument("--graph-parts", type=int, default=16)
+    ap.add_argument("--graph-mu", type=float, default=0.1,
+                    help="chemical potential (inside the chain's gap [-0.4, 0.4]; a cut chain "
+                         "segment can hold an edge state at exactly 0)")
     ap.add_argument("--batch", type=int, default=4000)
     ap.add_argument("--batch-prec", default="fp32_split",
                     choices=["fp32_split", "fp32_split_bf16"])
@@ -571,9 +574,9 @@ def run_graph(args):
     dense_ms = e0.elapsed_time(e1)
     G = Dref.clone()
     D = torch.empty_like(H)
-    tau, parts = args.graph_tau, args.graph_parts
+    tau, parts, mu = args.graph_tau, args.graph_parts, args.graph_mu
     for _ in range(max(1, args.warmup)):
-        D, ginfo = pkg.sp2_graph(H, G, tau, parts, 0.0, 1e-10, D=D)
+        D, ginfo = pkg.sp2_graph(H, G, tau, parts, mu, 1e-10, D=D)
     torch.cuda.synchronize()
     K = args.steps
     clocks = ClockSampler()
@@ -581,7 +584,7 @@ def run_graph(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
     for i in range(K):
         ev[2 * i].record()
-        pkg.sp2_graph(H, G, tau, parts, 0.0, 1e-10, D=D)
+        pkg.sp2_graph(H, G, tau, parts, mu, 1e-10, D=D)
         ev[2 * i + 1].record()
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -591,7 +594,7 @@ def run_graph(args):
     err = float(np.abs(Dn - Dr).max())
     # the oracle's graph solve on the host cores (same tau, parts, auxiliary)
     t0 = time.perf_counter()
-    P, _ = oracle.graph_density(H_np, Dr, tau, parts, 0.0, 1e-10)
+    P, _ = oracle.graph_density(H_np, Dr, tau, parts, mu, 1e-10)
     cpu_sec = time.perf_counter() - t0
     err_oracle = float(np.abs(Dn - P).max())
     # end to end: H and G in from pinned host memory, D out
@@ -602,7 +605,7 @@ def run_graph(args):
     e0.record()
     H.copy_(Hh, non_blocking=True)
     G.copy_(Gh, non_blocking=True)
-    pkg.sp2_graph(H, G, tau, parts, 0.0, 1e-10, D=D)
+    pkg.sp2_graph(H, G, tau, parts, mu, 1e-10, D=D)
     Dh.copy_(D, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
@@ -615,7 +618,7 @@ def run_graph(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f16x2 split, f32 accumulate",
             "data": "synthetic",
             "config": {"workload": f"graph-based divide and conquer: dimerized chain N={n} "
-                                   f"(t1=-1.0, t2=-0.6, gap 0.8), mu=0, {parts} regular-segment "
+                                   f"(t1=-1.0, t2=-0.6, gap 0.8), mu={mu}, {parts} regular-segment "
                                    f"cores, tau={tau} on a previous density matrix",
                        "parallelism": "one GPU"},
             "parts": ginfo, "d_check": {"max_abs_err_vs_dense_solve": err,
