@@ -26,6 +26,7 @@
 
 #include "progress_sp2.h"
 #include "sp2_launch.h"
+#include "sp2_tc.cuh"
 
 namespace {
 
@@ -92,12 +93,8 @@ __global__ void graph_symmetrize_kernel(double* __restrict__ P, int64_t n) {
   const int64_t T = (n + 31) / 32;
   // upper-triangle tile pairs (I <= J), one per block in a grid-stride loop
   for (int64_t t = blockIdx.x; t < T * (T + 1) / 2; t += gridDim.x) {
-    int64_t I = 0, r = t;
-    while (r >= T - I) {
-      r -= T - I;
-      ++I;
-    }
-    const int64_t J = I + r;
+    int I, J;
+    sp2::tc::tri_tile((int)t, (int)T, I, J);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
     for (int yy = ty; yy < 32; yy += 8) {
       const int64_t ri = I * 32 + yy, ci = J * 32 + tx;
