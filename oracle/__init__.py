@@ -20,6 +20,9 @@ computes, written from the paper (arXiv 2401.13772):
 * ``graph`` -- the graph-based divide-and-conquer density matrix of §VIII.B
   (threshold graph, core and core-halo partitions, submatrices, SP2 at a
   fixed chemical potential, core columns mapped back).
+* ``cheb`` -- the Chebyshev Fermi-operator expansion of §IV.B at a known
+  chemical potential and temperature: coefficients, the serial recursion, and
+  the Paterson-Stockmeyer nested form with its T_k-division coefficients.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 leg may import this package. It shares no code with the CUDA path and the
@@ -44,4 +47,14 @@ from .graph import (  # noqa: F401
     core_halo,
     sp2_fixed_mu,
     graph_density,
+)
+from .cheb import (  # noqa: F401
+    fermi,
+    scaled_hamiltonian,
+    cheb_coefficients,
+    ps_coefficients,
+    chebyshev_polynomials,
+    serial_chebyshev,
+    ps_evaluate,
+    fermi_operator,
 )
