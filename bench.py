@@ -87,16 +87,24 @@ def parse_args():
     ap.add_argument("--loop-mode", type=int, default=0,
                     help="0: device-driven WHILE graph; 1: plain launches (profilers)")
     ap.add_argument("--workload", default="dense",
-                    choices=["dense", "batched", "learned", "graph"],
+                    choices=["dense", "batched", "learned", "graph", "cheb"],
                     help="dense: one N = 4096 cube solve per step (headline); batched: 4000 "
                          "parts of 64..768 orbitals per step; learned: predictor training "
-                         "and evaluation; graph: graph-based divide and conquer of a chain")
+                         "and evaluation; graph: graph-based divide and conquer of a chain; "
+                         "cheb: finite-temperature Chebyshev expansion of the N = 4096 cube H")
     ap.add_argument("--graph-n", type=int, default=8192)
     ap.add_argument("--graph-tau", type=float, default=1e-5)
     ap.add_argument("--graph-parts", type=int, default=16)
     ap.add_argument("--graph-mu", type=float, default=0.1,
                     help="chemical potential (inside the chain's gap [-0.4, 0.4]; a cut chain "
                          "segment can hold an edge state at exactly 0)")
+    ap.add_argument("--cheb-mu", type=float, default=0.5,
+                    help="cheb workload: chemical potential (eV) of the Fermi function")
+    ap.add_argument("--cheb-beta", type=float, default=1.0,
+                    help="cheb workload: inverse temperature (1/eV)")
+    ap.add_argument("--cheb-k", type=int, default=16)
+    ap.add_argument("--cheb-m", type=int, default=16)
+    ap.add_argument("--cheb-prec", default="fp32_split", choices=["fp32_split", "fp32_split_bf16"])
     ap.add_argument("--batch", type=int, default=4000)
     ap.add_argument("--batch-prec", default="fp32_split",
                     choices=["fp32_split", "fp32_split_bf16"])
@@ -641,6 +649,114 @@ def run_graph(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cheb(args):
+    """Chebyshev Fermi-operator workload (§IV.B): the random-cube H of the dense
+    workload (`--sites` x 4 orbitals), f(H) at a known chemical potential and
+    temperature, L + 1 = k m terms in the Paterson-Stockmeyer form. One step =
+    one whole density matrix through the public call (Gershgorin bounds, one
+    read-back of them, coefficients on the host, every product on the GPU)."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2401_13772_gb300 as pkg
+    from paper_2401_13772_gb300.build import build
+    from workloads import cube_hamiltonian
+    build()
+    dev = torch.device("cuda", 0)
+    H_np, _ = cube_hamiltonian(args.sites, args.seed)
+    n = H_np.shape[0]
+    H = torch.from_numpy(H_np).to(dev)
+    D = torch.empty_like(H)
+    mu, beta, k, m, prec = args.cheb_mu, args.cheb_beta, args.cheb_k, args.cheb_m, args.cheb_prec
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    info = None
+    for _ in range(max(1, args.warmup)):
+        D, info = pkg.cheb_fermi(H, mu, beta, k, m, prec=prec, D=D)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+    clocks = ClockSampler()
+    clocks.start()
+    ms = []
+    for i in range(K):
+        flush.zero_()  # L2 flushed before each step (outside the events)
+        ev[2 * i].record()
+        pkg.cheb_fermi(H, mu, beta, k, m, prec=prec, D=D)
+        ev[2 * i + 1].record()
+        torch.cuda.synchronize()
+        ms.append(ev[2 * i].elapsed_time(ev[2 * i + 1]))
+    clk = clocks.stop()
+    sec = sum(ms) / K / 1e3
+    Dn = D.cpu().numpy()
+    # the oracle's whole solve on the host cores: accuracy and the CPU baseline
+    t0 = time.perf_counter()
+    ref = oracle.fermi_operator(H_np, mu, beta, k, m)
+    cpu_sec = time.perf_counter() - t0
+    err = float(np.abs(Dn - ref["D"]).max())
+    # diagonalization comparator of the paper's Chebyshev figure: FP64 eigh on
+    # the GPU (cuSOLVER through torch) and V f(w) V^T, timed once
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    w, V = torch.linalg.eigh(H)
+    f = 0.5 * (1.0 - torch.tanh(0.5 * beta * (w - mu)))
+    Dd = (V * f) @ V.T
+    e1.record()
+    torch.cuda.synchronize()
+    diag_ms = e0.elapsed_time(e1)
+    err_diag = float((D - Dd).abs().max())
+    # end to end: H in from pinned host memory, D out
+    Hh = torch.from_numpy(H_np).pin_memory()
+    Dh = torch.empty_like(Hh).pin_memory()
+    torch.cuda.synchronize()
+    e0.record()
+    H.copy_(Hh, non_blocking=True)
+    pkg.cheb_fermi(H, mu, beta, k, m, prec=prec, D=D)
+    Dh.copy_(D, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_sec = e0.elapsed_time(e1) / 1e3
+    products = info["products"]
+    flops = 2.0 * n ** 3 * products
+    peaks, src = load_peaks()
+    peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
+    slope = beta * 0.5 * (info["emax"] - info["emin"]) / 4.0
+    gate = 8.0 * 2.0 ** -23 * max(1.0, info["growth"]) * max(1.0, slope)
+    line = {"metric": METRIC, "value": 1.0 / sec, "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("f16x2 split, f32 accumulate" if prec == "fp32_split"
+                      else "bf16x3 split, f32 accumulate"),
+            "data": "synthetic",
+            "config": {"workload": f"Chebyshev Fermi operator (Paterson-Stockmeyer): random-cube "
+                                   f"tight-binding H, {args.sites} sites x 4 orbitals (N={n}), "
+                                   f"seed {args.seed}, mu={mu} eV, beta={beta}/eV, "
+                                   f"L+1={k * m} terms (k={k}, m={m})",
+                       "parallelism": "one GPU",
+                       "l2": "flushed before each step (256 MiB write, outside events)"},
+            "cheb": info, "serial_recursion_products": k * m - 1,
+            "d_check": {"max_abs_err_vs_oracle": err, "gate": gate,
+                        "max_abs_err_vs_eigh": err_diag,
+                        "truncation_last_coefficient": info["coef_last"]},
+            "diag_baseline": {"ms": diag_ms, "speedup": diag_ms / (sec * 1e3),
+                              "what": "torch.linalg.eigh (FP64, cuSOLVER) + V f V^T on the "
+                                      "same GPU"},
+            "tflops_algorithmic": flops / sec / 1e12,
+            "roofline": {"bound": "tensor", "achieved": flops / sec / 1e12, "peak": peak,
+                         "unit": "TFLOP/s", "frac": flops / sec / 1e12 / peak, "traffic": None,
+                         "kernel": "cheb_product_kernel (whole solve timed: bounds, host "
+                                   "coefficients, T_1, S_j pass and trace included)",
+                         "peak_source": f"fp16/bf16 dense, {src} burst",
+                         "flops_per_step": flops},
+            "cpu_baseline": {"value": 1.0 / cpu_sec, "unit": UNIT, "cores": cpu_cores(),
+                             "kind": "oracle", "sample": "one whole solve (same H, mu, beta, "
+                                                         "k, m; numpy FP64)"},
+            "e2e": {"value": 1.0 / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": int(H_np.nbytes),
+                    "d2h_bytes_per_step": int(H_np.nbytes)},
+            "gpu_launches": info["launches"] * K, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -654,6 +770,9 @@ def main():
         return
     if args.workload == "graph":
         run_graph(args)
+        return
+    if args.workload == "cheb":
+        run_cheb(args)
         return
     import numpy as np
     import torch

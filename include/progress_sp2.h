@@ -319,6 +319,92 @@ progress_status_t progress_sp2_graph(const double* dH, const double* dG, int64_t
                                      void* stream);
 
 /*
+ * Finite-temperature density matrix by the Chebyshev Fermi-operator expansion
+ * (§IV.B) in the Paterson-Stockmeyer form (Eqs. 7-11):
+ *   D = f(H),  f(e) = 1 / (1 + exp(beta (e - mu)))  (§III, at a known mu),
+ *   Ht = (H - a I) / b with a, b the midpoint and half-width of the bounds,
+ *   f(b x + a) ~ sum_{n<=L} c_n T_n(x), L + 1 = k m, c_n from interpolation at
+ *   the 2 (L + 1) Chebyshev-Gauss nodes (no damping kernel),
+ *   D = S_0 + T_k (S_1 + T_k (... + T_k S_{m-1})), S_j = sum_{i<k} d_ij T_i,
+ *   with d_ij from dividing the series by T_k (T_n = 2 T_k T_{n-k} - T_{|2k-n|}).
+ * T_2..T_k come from T_n = 2 T_a T_b - T_{a-b} (a = ceil(n/2), b = floor(n/2)),
+ * all T_n of one doubling level in one launch; then the m - 1 nested products.
+ * Matrix products: (k - 1) + (m - 1) (k - 2 when m = 1), against L for the
+ * serial recursion of Eq. 6.
+ *   dH        device, n x n FP64 symmetric, read only
+ *   n         1 <= n <= 32768
+ *   mu, beta  chemical potential (finite) and inverse temperature (finite,
+ *             >= 0), in the units of H
+ *   k, m      1..64 each. Stability: the nested sums grow like
+ *             info->growth; keep k >= m (k of about 2 sqrt(L) or more) for a
+ *             sharp Fermi function
+ *   prec      PROGRESS_FP32_SPLIT: fp16 hi+lo operand slices on the tensor
+ *             cores, FP32 accumulate (leading group summed every 64 k);
+ *             PROGRESS_FP32_SPLIT_BF16: bf16 hi+mid+lo slices (six products per
+ *             tile step instead of three). Any other value: EINVAL. The error
+ *             of D is about (growth) (beta b / 4) 2^-23 with b the half-width
+ *             of the bounds: the Fermi function's slope times the FP32-class
+ *             product error
+ *   h_bounds  HOST, 2 doubles {emin, emax} enclosing the spectrum, or NULL for
+ *             the Gershgorin bounds (one device-to-host read of 2 doubles)
+ *   dD        device, n x n FP64, written (must not be dH)
+ *   info      host, optional: bounds used, Tr D, growth, products, launches,
+ *             |c_L| (truncation indicator)
+ * Synchronizes the stream before it returns (the work buffers of a previous
+ * call on the stream are reused; info is read back).
+ * Errors: EINVAL (sizes, k, m, prec, beta < 0, non-finite mu or bounds, NULL
+ * pointers, dD == dH), EUNSUPPORTED (not an sm_10x GPU), ENOMEM,
+ * ETIMEOUT (a bounded device wait gave up; D is not valid), ECUDA.
+ */
+typedef struct {
+  double emin, emax;    /* bounds used (before a zero-width interval is widened by 1) */
+  double trace;         /* Tr D: the electron count at mu (spin factor excluded) */
+  double growth;        /* sum over j of sum_i |d_ij|: bound on the nested sums' norms */
+  double coef_last;     /* |c_L|, the last expansion coefficient */
+  int32_t products;     /* matrix products performed */
+  int32_t launches;     /* kernel launches */
+} progress_cheb_info_t;
+
+progress_status_t progress_cheb_fermi(const double* dH, int64_t n, double mu, double beta,
+                                      int32_t k, int32_t m, int32_t prec,
+                                      const double* h_bounds, double* dD,
+                                      progress_cheb_info_t* info, void* stream);
+
+/*
+ * The schedule progress_cheb_fermi runs for bounds {emin, emax} (host only, no
+ * GPU): every matrix lives in a stack slot (T_i in slot i - 1, S_j in slot
+ * k + j, nested results in slots k + m and k + m + 1). Product q computes
+ *   C = alpha sab (A B) + beta se E + gamma I   (E term absent if e < 0)
+ * from the stored (scaled) A, B, E and stores C * inv_sc in slot c, or writes
+ * D (c < 0). Launch order: T_1 = (H - a I) / b in slot 0, the T-level product
+ * launches, the S_j pass (S_j stored as S_j * inv_s[j]; with m = 1 it writes D),
+ * then the nested product launches; products sharing a launch index read only
+ * slots written by earlier launches.
+ *   cap     capacity of prods / params in products ((k - 1) + (m - 1) suffice)
+ *   prods   host int32 [cap][5]: a, b, e, c, launch index
+ *   params  host float [cap][6]: alpha, sab, beta, se, gamma, inv_sc
+ *   dcoef   host double [k m]: d_ij at i m + j;  inv_s: host double [m]
+ *   ab      host double [2]: a, b;  counts: host int32 [4]: products, product
+ *           launches, slots, T-level products
+ * Errors: EINVAL (k, m, mu, beta, bounds, NULL pointers, cap too small).
+ */
+/*
+ * Copy one operand slice of one stack slot of the last progress_cheb_fermi
+ * solve on `stream` (ld x ld uint16, ld = n rounded up to 128, row-major) into
+ * host_out, for inspection of the intermediate T_i, S_j and nested results
+ * (slot layout as in progress_cheb_plan; slice 0 = hi, 1 = lo (fp16) or mid,
+ * 2 = lo (bf16); value = scale * (hi + lo / 2048) for fp16, scale * (hi + mid +
+ * lo) for bf16, the slot's scale from the plan). Synchronizes the stream.
+ * Errors: EINVAL (no solve on the stream, slot or slice out of range, NULL).
+ */
+progress_status_t progress_cheb_slot(int32_t slot, int32_t slice, uint16_t* host_out,
+                                     void* stream);
+
+progress_status_t progress_cheb_plan(int32_t k, int32_t m, double mu, double beta, double emin,
+                                     double emax, int32_t cap, int32_t* prods, float* params,
+                                     double* dcoef, double* inv_s, double* ab, int32_t* counts);
+
+/*
  * Features of the learned predictor, 37 floats per instance (device output
  * [batch][37]): Gershgorin emin/w, emax/w (w = emax - emin, §VIII.A),
  * Tr H/(n w), ||H||_F/(sqrt(n) w), a 32-bin histogram of diag(H) over
@@ -380,7 +466,7 @@ progress_status_t progress_sp2_query(void* stream, progress_info_t* info);
  */
 int32_t progress_sp2_history(void* stream, double* idem, double* margin, int32_t cap);
 
-/* Free the cached work spaces (dense, batched and graph solves) of `stream` on the
+/* Free the cached work spaces (dense, batched, graph and Chebyshev solves) of `stream` on the
  * current device (synchronizes it). */
 progress_status_t progress_release(void* stream);
 

@@ -245,6 +245,79 @@ def sp2_graph(H, G, tau, nparts, mu, tol, D=None, prec="fp32_split", maxiter=100
     return D, info.to_dict()
 
 
+def cheb_fermi(H, mu, beta, k, m, prec="fp32_split", bounds=None, D=None, stream=None):
+    """Finite-temperature density matrix f(H), f(e) = 1 / (1 + exp(beta (e - mu))),
+    by the Chebyshev expansion of §IV.B in the Paterson-Stockmeyer form with
+    L + 1 = k m terms ((k - 1) + (m - 1) matrix products on the tensor cores).
+    prec: "fp32_split" (fp16 hi+lo slices) or "fp32_split_bf16" (bf16 hi+mid+lo).
+    bounds: (emin, emax) enclosing the spectrum, or None for Gershgorin.
+    H: square float64 CUDA tensor. Returns (D, info dict)."""
+    import torch
+    if not (isinstance(H, torch.Tensor) and H.is_cuda and H.dtype == torch.float64 and
+            H.dim() == 2 and H.shape[0] == H.shape[1] and H.is_contiguous()):
+        raise TypeError("H must be a square contiguous float64 CUDA tensor")
+    codes = {"fp32_split": FP32_SPLIT, "fp32_split_bf16": FP32_SPLIT_BF16}
+    if prec not in codes:
+        raise ValueError(f"prec must be one of {sorted(codes)}")
+    n = H.shape[0]
+    if D is None:
+        D = torch.empty_like(H)
+    hb = None
+    if bounds is not None:
+        hb = (ctypes.c_double * 2)(float(bounds[0]), float(bounds[1]))
+    info = _lib.ChebInfo()
+    with torch.cuda.device(H.device):
+        check(load().progress_cheb_fermi(
+            ctypes.c_void_p(H.data_ptr()), n, float(mu), float(beta), int(k), int(m),
+            int(codes[prec]), ctypes.cast(hb, ctypes.c_void_p) if hb is not None else None,
+            ctypes.c_void_p(D.data_ptr()), ctypes.byref(info), _stream_ptr(stream)))
+    return D, info.to_dict()
+
+
+def cheb_slot(n, slot, prec="fp32_split", scale=1.0, stream=None):
+    """Value (float64 numpy, n x n) of one stack slot of the last cheb_fermi solve
+    on the stream, decoded from its slices and multiplied by scale."""
+    import numpy as np
+    ld = (n + 127) // 128 * 128
+    ns = 2 if prec == "fp32_split" else 3
+    planes = []
+    for j in range(ns):
+        buf = np.empty((ld, ld), dtype=np.uint16)
+        check(load().progress_cheb_slot(int(slot), j, ctypes.c_void_p(buf.ctypes.data),
+                                        _stream_ptr(stream)))
+        planes.append(buf)
+    if ns == 2:
+        v = (planes[0].view(np.float16).astype(np.float64) +
+             planes[1].view(np.float16).astype(np.float64) / 2048.0)
+    else:
+        def bf(u):
+            return (u.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        v = bf(planes[0]) + bf(planes[1]) + bf(planes[2])
+    return scale * v[:n, :n]
+
+
+def cheb_plan(k, m, mu, beta, emin, emax):
+    """The product schedule cheb_fermi runs for the bounds (emin, emax), computed by
+    the library on the host (no GPU). Returns a dict of numpy arrays: prods [P, 5]
+    (a, b, e, c, launch), params [P, 6] (alpha, sab, beta, se, gamma, inv_sc),
+    d [k, m], inv_s [m], a, b, product_launches, slots, t_products."""
+    import numpy as np
+    cap = max(1, (k - 1) + (m - 1))
+    prods = np.zeros((cap, 5), dtype=np.int32)
+    params = np.zeros((cap, 6), dtype=np.float32)
+    d = np.zeros(k * m)
+    inv_s = np.zeros(m)
+    ab = np.zeros(2)
+    counts = np.zeros(4, dtype=np.int32)
+    check(load().progress_cheb_plan(int(k), int(m), float(mu), float(beta), float(emin),
+                                    float(emax), cap, *(ctypes.c_void_p(x.ctypes.data) for x in
+                                                        (prods, params, d, inv_s, ab, counts))))
+    np_ = int(counts[0])
+    return {"prods": prods[:np_], "params": params[:np_], "d": d.reshape(k, m), "inv_s": inv_s,
+            "a": float(ab[0]), "b": float(ab[1]), "product_launches": int(counts[1]),
+            "slots": int(counts[2]), "t_products": int(counts[3])}
+
+
 def history(stream=None, cap=256):
     """(idem, margin) numpy arrays of the last solve on the stream: idem[k] =
     |Tr X_k^2 - Tr X_k|, margin[k] = signed branch-rule margin of product k."""

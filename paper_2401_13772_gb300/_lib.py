@@ -67,6 +67,18 @@ class GraphInfo(ctypes.Structure):
                 "sub_elements": self.sub_elements}
 
 
+class ChebInfo(ctypes.Structure):
+    _fields_ = [("emin", ctypes.c_double), ("emax", ctypes.c_double),
+                ("trace", ctypes.c_double), ("growth", ctypes.c_double),
+                ("coef_last", ctypes.c_double), ("products", ctypes.c_int32),
+                ("launches", ctypes.c_int32)]
+
+    def to_dict(self):
+        return {"emin": self.emin, "emax": self.emax, "trace": self.trace,
+                "growth": self.growth, "coef_last": self.coef_last,
+                "products": self.products, "launches": self.launches}
+
+
 class BatchTune(ctypes.Structure):
     _fields_ = [("tile_n", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("share", ctypes.c_int32), ("ncand", ctypes.c_int32),
@@ -99,6 +111,12 @@ SIGNATURES = {
                                                  ctypes.c_int32, ctypes.POINTER(BatchTune), _P]),
     "progress_sp2_graph": (ctypes.c_int, [_P, _P, _I64, _D, ctypes.c_int32, _D, _D, _P,
                                           ctypes.POINTER(Opts), ctypes.POINTER(GraphInfo), _P]),
+    "progress_cheb_fermi": (ctypes.c_int, [_P, _I64, _D, _D, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, _P, _P, ctypes.POINTER(ChebInfo),
+                                           _P]),
+    "progress_cheb_slot": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "progress_cheb_plan": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _D, _D, _D, _D,
+                                          ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
     "progress_features": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P]),
     "progress_trace_hd": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
     "progress_mlp_param_count": (ctypes.c_int32, [ctypes.c_int32] * 3),

@@ -457,6 +457,7 @@ progress_status_t progress_release(void* stream) {
   CK(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
   sp2::batched_release(dev, (cudaStream_t)stream, false);
   sp2::graph_release(dev, (cudaStream_t)stream, false);
+  sp2::cheb_release(dev, (cudaStream_t)stream, false);
   Workspace* w = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -476,6 +477,7 @@ progress_status_t progress_release_all(void) {
   CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
   sp2::batched_release(dev, nullptr, true);
   sp2::graph_release(dev, nullptr, true);
+  sp2::cheb_release(dev, nullptr, true);
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto it = g_ws.begin(); it != g_ws.end();) {
     if (it->first.first == dev) {

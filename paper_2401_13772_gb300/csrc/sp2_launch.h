@@ -67,10 +67,11 @@ int fp64_tile_count(int ld);
 // Record the text that progress_last_error() returns on this thread.
 void set_last_error(const char* what);
 
-// Free the batched and graph work spaces of (dev, stream), or of every stream
+// Free the batched, graph and Chebyshev work spaces of (dev, stream), or of every stream
 // of dev; the caller has synchronized the stream (device).
 void batched_release(int dev, cudaStream_t s, bool all_streams);
 void graph_release(int dev, cudaStream_t s, bool all_streams);
+void cheb_release(int dev, cudaStream_t s, bool all_streams);
 int split_tile_count(int ld);
 
 }  // namespace sp2

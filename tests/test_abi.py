@@ -61,6 +61,30 @@ def test_struct_sizes_match_header_layout():
     # progress_batch_tune_t: 4 int32, int32 cand[16][3], float ms[16]
     assert ctypes.sizeof(_lib.BatchTune) == 4 * 4 + 16 * 3 * 4 + 16 * 4
     assert _lib.BatchTune.ms.offset == 16 + 16 * 3 * 4
+    # progress_cheb_info_t: 5 double, 2 int32
+    assert ctypes.sizeof(_lib.ChebInfo) == 5 * 8 + 2 * 4
+    assert _lib.ChebInfo.products.offset == 40
+
+
+def test_cheb_argument_errors(lib):
+    from paper_2401_13772_gb300 import _lib
+    P = ctypes.c_void_p
+    ci = _lib.ChebInfo()
+    args = dict(n=64, mu=0.0, beta=1.0, k=8, m=8, prec=_lib.FP32_SPLIT)
+
+    def call(dH=P(16), dD=P(32), **kw):
+        a = dict(args, **kw)
+        return lib.progress_cheb_fermi(dH, a["n"], a["mu"], a["beta"], a["k"], a["m"],
+                                       a["prec"], None, dD, ctypes.byref(ci), None)
+    assert call(n=0) == _lib.EINVAL
+    assert call(k=0) == _lib.EINVAL and call(m=65) == _lib.EINVAL
+    assert b"k and m" in lib.progress_last_error()
+    assert call(beta=-1.0) == _lib.EINVAL
+    assert call(mu=float("nan")) == _lib.EINVAL
+    assert call(prec=_lib.MIXED_FP16) == _lib.EINVAL
+    assert b"prec" in lib.progress_last_error()
+    assert call(dD=P(16)) == _lib.EINVAL
+    assert call(dH=None) == _lib.EINVAL
 
 
 def test_batched_argument_errors(lib):
