@@ -21,8 +21,8 @@
 //                        runs them on concurrent streams; here they share one
 //                        launch). Then the m - 1 nested products
 //                        P_j = S_j + T_k P_{j+1}; the last writes D in FP64.
-//   cheb_sum_kernel      every S_j in one pass over T_1..T_{k-1} (the sums
-//                        are independent, Eq. 9)
+//   cheb_sum16_kernel /  every S_j in one pass over T_1..T_{k-1} (the sums
+//   cheb_sum_kernel      are independent, Eq. 9); the first for k, m <= 16
 //
 // Every matrix is a polynomial in Ht, so all of them are symmetric and
 // commute: a product tile (I, J), I <= J, reads the row panels I of A and J
@@ -450,6 +450,71 @@ __global__ void __launch_bounds__(EW_THREADS)
   }
 }
 
+// The same pass for k, m <= 16 with the coefficients as kernel parameters (a
+// zero-padded 16 x 16 table in the constant bank: every multiply-add of the
+// fully unrolled loops takes its coefficient as an immediate constant operand)
+// and two neighbouring elements per thread (32-bit slice loads and stores).
+constexpr int SUM_K = 16;
+struct SumTable {
+  float d[SUM_K * SUM_K];  // d_ij at i SUM_K + j, zero outside i < k, j < m
+  float inv_s[SUM_K];
+};
+
+template <int F>
+__global__ void __launch_bounds__(EW_THREADS)
+    cheb_sum16_kernel(Pool pool, int ld, int k, int m, const __grid_constant__ SumTable tab,
+                      double* __restrict__ D, int64_t n, const int* __restrict__ gerr) {
+  if (*(volatile const int*)gerr) return;  // no barrier below: a per-thread exit is safe
+  const size_t area = (size_t)ld * ld;
+  const size_t pairs = area / 2;
+  for (size_t q = (size_t)blockIdx.x * EW_THREADS + threadIdx.x; q < pairs;
+       q += (size_t)gridDim.x * EW_THREADS) {
+    const size_t e = 2 * q;  // ld is even: e and e + 1 share a row
+    const int64_t r = (int64_t)(e / ld), c = (int64_t)(e - (size_t)r * ld);
+    float t0[SUM_K], t1[SUM_K];
+    t0[0] = (r == c) ? 1.0f : 0.0f;
+    t1[0] = (r == c + 1) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int i = 1; i < SUM_K; ++i) {
+      t0[i] = 0.0f;
+      t1[i] = 0.0f;
+      if (i < k) {
+        const size_t o = (size_t)(i - 1) * area + e;
+        const uint32_t h = *reinterpret_cast<const uint32_t*>(pool.s[0] + o);
+        const uint32_t l = *reinterpret_cast<const uint32_t*>(pool.s[1] + o);
+        const uint32_t w = fmt_bf16(F) ? *reinterpret_cast<const uint32_t*>(pool.s[2] + o) : 0u;
+        t0[i] = join_value<F>((uint16_t)(h & 0xffffu), (uint16_t)(l & 0xffffu),
+                              (uint16_t)(w & 0xffffu));
+        t1[i] = join_value<F>((uint16_t)(h >> 16), (uint16_t)(l >> 16), (uint16_t)(w >> 16));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < SUM_K; ++j) {
+      if (j < m) {
+        float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < SUM_K; ++i) {
+          a0 += tab.d[i * SUM_K + j] * t0[i];
+          a1 += tab.d[i * SUM_K + j] * t1[i];
+        }
+        if (m == 1) {
+          if (r < n && c < n) D[r * n + c] = (double)a0;
+          if (r < n && c + 1 < n) D[r * n + c + 1] = (double)a1;
+        } else {
+          uint16_t x0, x1, x2, y0, y1, y2;
+          split_value_f<F>(a0 * tab.inv_s[j], x0, x1, x2);
+          split_value_f<F>(a1 * tab.inv_s[j], y0, y1, y2);
+          const size_t o = (size_t)(k + j) * area + e;
+          *reinterpret_cast<uint32_t*>(pool.s[0] + o) = (uint32_t)x0 | ((uint32_t)y0 << 16);
+          *reinterpret_cast<uint32_t*>(pool.s[1] + o) = (uint32_t)x1 | ((uint32_t)y1 << 16);
+          if (fmt_bf16(F))
+            *reinterpret_cast<uint32_t*>(pool.s[2] + o) = (uint32_t)x2 | ((uint32_t)y2 << 16);
+        }
+      }
+    }
+  }
+}
+
 __global__ void cheb_trace_kernel(const double* __restrict__ D, int64_t n, double* out) {
   __shared__ double s[EW_THREADS / 32];
   double v = 0.0;
@@ -791,8 +856,19 @@ progress_status_t run(const double* dH, int64_t n, double mu, double beta, int k
     ++launches;
     first = end;
   }
-  cheb_sum_kernel<F><<<ew_blocks, EW_THREADS, 0, s>>>(pool, ld, k, m, w->dcoef, w->inv_s, dD, n,
-                                                      w->err);
+  if (k <= SUM_K && m <= SUM_K) {
+    SumTable tab;
+    memset(&tab, 0, sizeof tab);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < m; ++j) tab.d[i * SUM_K + j] = dcoef[(size_t)i * m + j];
+    for (int j = 0; j < m; ++j) tab.inv_s[j] = inv_s[j];
+    const unsigned pair_blocks = (unsigned)std::min<size_t>(
+        EW_BLOCKS, ((size_t)ld * ld / 2 + EW_THREADS - 1) / EW_THREADS);
+    cheb_sum16_kernel<F><<<pair_blocks, EW_THREADS, 0, s>>>(pool, ld, k, m, tab, dD, n, w->err);
+  } else {
+    cheb_sum_kernel<F><<<ew_blocks, EW_THREADS, 0, s>>>(pool, ld, k, m, w->dcoef, w->inv_s, dD,
+                                                        n, w->err);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return ccuda(e, "cheb_sum launch");
   ++launches;
   for (int q = t_products; q < nprod; ++q) {
