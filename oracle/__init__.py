@@ -20,6 +20,8 @@ computes, written from the paper (arXiv 2401.13772):
 * ``graph`` -- the graph-based divide-and-conquer density matrix of §VIII.B
   (threshold graph, core and core-halo partitions, submatrices, SP2 at a
   fixed chemical potential, core columns mapped back).
+* ``sparse`` -- thresholded SP2 (Listing 1's cutoff tau: each product and each
+  2X - X^2 update drops the elements below tau).
 * ``cheb`` -- the Chebyshev Fermi-operator expansion of §IV.B at a known
   chemical potential and temperature: coefficients, the serial recursion, and
   the Paterson-Stockmeyer nested form with its T_k-division coefficients.
@@ -58,3 +60,4 @@ from .cheb import (  # noqa: F401
     ps_evaluate,
     fermi_operator,
 )
+from .sparse import prune, sp2_thresholded  # noqa: F401
