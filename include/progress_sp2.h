@@ -98,7 +98,13 @@ typedef struct {
                            3 = exact products of BF16 fixed-point digits on the tensor
                            cores (Ozaki scheme; ~2^-40 absolute accuracy; n <= 8192, else
                            PROGRESS_EUNSUPPORTED) */
-  int32_t reserved[3];  /* must be zero */
+  float tau;            /* cutoff of thresholded SP2 (Listing 1's tau): every product X*X and
+                           every 2X - X^2 drops the elements with |x| < tau; X0 is not
+                           pruned. 0 (default) = dense. tau > 0 needs prec FP32_SPLIT or
+                           FP32_SPLIT_BF16 (else EINVAL); the product then skips every
+                           128 x 128 block pair of X that holds no non-zero and leaves a
+                           result tile that stays zero unwritten */
+  int32_t reserved[2];  /* must be zero */
 } progress_opts_t;
 
 /* Result of one solve, read back from the device by the calls that take it. */
@@ -113,6 +119,9 @@ typedef struct {
   double trace;          /* Tr D */
   double idempotency;    /* |Tr D^2 - Tr D| of the returned D */
   uint64_t bits[4];      /* branch of product k is bit (k % 64) of bits[k / 64]; 1 = 2X - X^2 */
+  uint64_t kblocks;      /* thresholded SP2 (tau > 0): 128 x 128 x 64 tile steps streamed over
+                            all products (a dense product streams T (T + 1) / 2 x ld / 64 of
+                            them, ld = n rounded up to 128, T = ld / 128); 0 otherwise */
 } progress_info_t;
 
 /* Fill *opts with the defaults listed above. */

@@ -64,7 +64,7 @@ def gershgorin_bounds(H, out=None, stream=None):
 
 
 def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None, emax=None,
-              loop_mode=0, loop_events=None, slice_fixed=0, fp64_impl=0):
+              loop_mode=0, loop_events=None, slice_fixed=0, fp64_impl=0, tau=0.0):
     o = Opts()
     load().progress_opts_default(ctypes.byref(o))
     o.prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
@@ -76,6 +76,7 @@ def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None
     o.loop_mode = int(loop_mode)
     o.slice_fixed = int(slice_fixed)
     o.fp64_impl = int(fp64_impl)
+    o.tau = float(tau)
     if loop_events is not None:
         # torch.cuda.Event pair, already created (recorded once)
         o.loop_events[0] = loop_events[0].cuda_event
@@ -99,8 +100,8 @@ def sp2_dense(H, nocc, tol, D=None, stream=None):
 
 def sp2_dense_ex(H, nocc, tol, D=None, info=True, stream=None, raise_on_status=True, **opts):
     """SP2 solve with options (prec, rule, fp64_prefix, maxiter, emin, emax,
-    loop_mode, loop_events). With info=True it synchronizes and returns
-    (D, info dict)."""
+    loop_mode, loop_events, slice_fixed, fp64_impl, tau). With info=True it
+    synchronizes and returns (D, info dict)."""
     import torch
     _check_matrix(H, "H")
     if D is None:

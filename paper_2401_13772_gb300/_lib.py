@@ -27,7 +27,7 @@ class Opts(ctypes.Structure):
                 ("emin", ctypes.c_double), ("emax", ctypes.c_double),
                 ("loop_mode", ctypes.c_int32), ("slice_fixed", ctypes.c_int32),
                 ("loop_events", ctypes.c_void_p * 2), ("fp64_impl", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("tau", ctypes.c_float), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Info(ctypes.Structure):
@@ -35,7 +35,7 @@ class Info(ctypes.Structure):
                 ("converged", ctypes.c_int32), ("phase_iters", ctypes.c_int32 * 3),
                 ("emin", ctypes.c_double), ("emax", ctypes.c_double),
                 ("trace", ctypes.c_double), ("idempotency", ctypes.c_double),
-                ("bits", ctypes.c_uint64 * 4)]
+                ("bits", ctypes.c_uint64 * 4), ("kblocks", ctypes.c_uint64)]
 
     def to_dict(self):
         bits = [(self.bits[k // 64] >> (k % 64)) & 1 for k in range(self.iters)]
@@ -43,7 +43,7 @@ class Info(ctypes.Structure):
                 "iters": self.iters, "converged": bool(self.converged),
                 "phase_iters": list(self.phase_iters), "emin": self.emin,
                 "emax": self.emax, "trace": self.trace,
-                "idempotency": self.idempotency, "bits": bits}
+                "idempotency": self.idempotency, "bits": bits, "kblocks": self.kblocks}
 
 
 class BatchEx(ctypes.Structure):

@@ -45,6 +45,7 @@ struct Workspace {
   int x64_cap = 0;      // ld of the FP64 ping-pong buffers (0 = none)
   int slices_cap = 0;   // slices per set that are allocated
   int digits_cap = 0;   // ld of the digit planes (0 = none)
+  size_t flags_cap = 0; // bytes of each tile-flag array (thresholded SP2)
   sp2::DevBuffers buf{};
   sp2::State* h_state = nullptr;  // pinned host mirror for readback
   cudaStream_t cap_stream = nullptr;
@@ -52,6 +53,7 @@ struct Workspace {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int g_ld = -1, g_prec = -1, g_fmt = -1, g_df = -1, g_oz = -1;
+  float g_tau = -1.0f;
 };
 
 std::mutex g_mu;
@@ -63,6 +65,7 @@ void free_graph(Workspace* w) {
   w->exec = nullptr;
   w->graph = nullptr;
   w->g_ld = w->g_prec = w->g_fmt = w->g_df = w->g_oz = -1;
+  w->g_tau = -1.0f;
 }
 
 void free_matrices(Workspace* w) {
@@ -82,6 +85,27 @@ void free_matrices(Workspace* w) {
   w->buf.partials = nullptr;
   w->buf.max_partials = 0;
   w->x64_cap = w->slices_cap = w->ld_cap = w->digits_cap = 0;
+  for (int k = 0; k < 2; ++k) {
+    if (w->buf.tflags[k]) cudaFree(w->buf.tflags[k]);
+    w->buf.tflags[k] = nullptr;
+  }
+  w->flags_cap = 0;
+}
+
+// Tile-flag arrays of thresholded SP2 for order ld.
+progress_status_t ensure_flags(Workspace* w, int ld) {
+  const size_t t = (size_t)(ld / 128);
+  if (w->flags_cap >= t * t && w->buf.tflags[0]) return PROGRESS_OK;
+  CK(cudaStreamSynchronize(w->stream), "cudaStreamSynchronize");
+  free_graph(w);  // the loop graph holds the old pointers
+  for (int k = 0; k < 2; ++k) {
+    if (w->buf.tflags[k]) cudaFree(w->buf.tflags[k]);
+    w->buf.tflags[k] = nullptr;
+  }
+  w->flags_cap = 0;
+  for (int k = 0; k < 2; ++k) CK(cudaMalloc(&w->buf.tflags[k], t * t), "tile flag allocation");
+  w->flags_cap = t * t;
+  return PROGRESS_OK;
 }
 
 void free_workspace(Workspace* w) {
@@ -190,7 +214,7 @@ progress_status_t queue_steps(Workspace* w, const sp2::SolveParams& p, unsigned 
 
 progress_status_t build_graph(Workspace* w, const sp2::SolveParams& p) {
   if (w->exec && w->g_ld == p.ld && w->g_prec == p.prec && w->g_fmt == p.slice_fmt &&
-      w->g_df == p.df64 && w->g_oz == p.oz)
+      w->g_df == p.df64 && w->g_oz == p.oz && w->g_tau == p.tau)
     return PROGRESS_OK;
   free_graph(w);
   cudaGraph_t g = nullptr;
@@ -239,6 +263,7 @@ progress_status_t build_graph(Workspace* w, const sp2::SolveParams& p) {
   w->g_fmt = p.slice_fmt;
   w->g_df = p.df64;
   w->g_oz = p.oz;
+  w->g_tau = p.tau;
   return PROGRESS_OK;
 }
 
@@ -255,6 +280,7 @@ void fill_info(const sp2::State& s, progress_info_t* info) {
   info->trace = s.t1;
   info->idempotency = s.idem;
   for (int i = 0; i < 4; ++i) info->bits[i] = s.bits[i];
+  info->kblocks = s.kblocks;
 }
 
 progress_status_t query(Workspace* w, progress_info_t* info) {
@@ -352,6 +378,10 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   if (o.fp64_prefix < 0) return fail(PROGRESS_EINVAL, "fp64_prefix must be >= 0");
   if (o.loop_mode != 0 && o.loop_mode != 1) return fail(PROGRESS_EINVAL, "loop_mode must be 0 or 1");
   if (o.slice_fixed != 0 && o.slice_fixed != 1) return fail(PROGRESS_EINVAL, "slice_fixed must be 0 or 1");
+  if (!(o.tau >= 0.0f) || !isfinite(o.tau)) return fail(PROGRESS_EINVAL, "tau must be finite and >= 0");
+  if (o.tau > 0.0f && (o.prec != PROGRESS_FP32_SPLIT || o.slice_fixed))
+    return fail(PROGRESS_EINVAL,
+                "tau > 0 needs prec FP32_SPLIT or FP32_SPLIT_BF16 with floating slices");
   if (!isnan(o.emin) || !isnan(o.emax)) {
     if (isnan(o.emin) || isnan(o.emax) || !(o.emax > o.emin))
       return fail(PROGRESS_EINVAL, "bounds override needs emin < emax (both set)");
@@ -380,6 +410,10 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   const int nslices = o.prec == PROGRESS_FP64 ? 0 : sp2::fmt_slices(fmt);
   st = ensure_buffers(w, ld, need_x64, nslices, oz != 0);
   if (st != PROGRESS_OK) return st;
+  if (o.tau > 0.0f) {
+    st = ensure_flags(w, ld);
+    if (st != PROGRESS_OK) return st;
+  }
 
   sp2::SolveParams p;
   memset(&p, 0, sizeof p);
@@ -396,10 +430,12 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   p.tol = tol;
   p.emin_override = o.emin;
   p.emax_override = o.emax;
+  p.tau = o.tau;
 
   CK(sp2::launch_init(w->buf, p, s), "init launch");
   CK(sp2::launch_gershgorin(dH, n, w->buf, nullptr, s), "gershgorin launch");
   CK(sp2::launch_x0(dH, w->buf, p, s), "x0 launch");
+  if (p.tau > 0.0f) CK(sp2::launch_tile_flags(dH, n, ld, w->buf, s), "tile flag launch");
   if (o.loop_events[0]) CK(cudaEventRecord((cudaEvent_t)o.loop_events[0], s), "event record");
   if (o.loop_mode == 0) {
     st = build_graph(w, p);

@@ -56,6 +56,7 @@ struct State {
   int judge_fail;
   double judge_delta;
   double y_mu;  // PROGRESS_RULE_MU: the chemical potential under the same map as X_k
+  unsigned long long kblocks;  // thresholded SP2: 64-wide k-blocks streamed (all products)
   unsigned long long bits[4];
   double idem_hist[kMaxHist];
   double margin_hist[kMaxHist];

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(kEwThreads) x0_kernel(const double* __restrict
   const int64_t n = st->n;
   const int ld = st->ld;
   const double emax = st->emax, width = st->emax - st->emin;
+  const double inv_w = 1.0 / width;  // one division per thread (FP64 division is slow here)
   const bool df64 = st->df64 != 0;
   float* Xf = reinterpret_cast<float*>(X);
   const size_t plane = (size_t)ld * ld;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kEwThreads) x0_kernel(const double* __restrict
       double x = 0.0;
       if (r < n && c < n) {
         const double h = H[r * n + c];
-        x = ((r == c) ? (emax - h) : -h) / width;
+        x = ((r == c) ? (emax - h) : -h) * inv_w;
         if (r == c) tr += x;
         fr += x * x;
       }
@@ -234,6 +235,35 @@ cudaError_t launch_x0(const double* H, const DevBuffers& b, const SolveParams& p
     default:
       return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// One CTA per 128 x 128 tile (I, J): flag 1 if X0 may be non-zero there (a
+// diagonal tile inside the matrix, or a non-zero of H), and "unknown content"
+// for the other slice set, whose buffers have not been written yet.
+__global__ void __launch_bounds__(kEwThreads)
+    tile_flags_kernel(const double* __restrict__ H, int64_t n, int T, uint8_t* __restrict__ f0,
+                      uint8_t* __restrict__ f1) {
+  const int I = blockIdx.x / T, J = blockIdx.x - (blockIdx.x / T) * T;
+  const int64_t r0 = (int64_t)I * 128, c0 = (int64_t)J * 128;
+  int any = (I == J && r0 < n) ? 1 : 0;
+  if (!any) {
+    for (int e = threadIdx.x; e < 128 * 128; e += kEwThreads) {
+      const int64_t r = r0 + (e >> 7), c = c0 + (e & 127);
+      if (r < n && c < n && H[r * n + c] != 0.0) any = 1;
+    }
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    f0[blockIdx.x] = (uint8_t)(any ? 1 : 0);
+    f1[blockIdx.x] = 1;
+  }
+}
+
+cudaError_t launch_tile_flags(const double* H, int64_t n, int ld, const DevBuffers& b,
+                              cudaStream_t s) {
+  const int T = ld / 128;
+  tile_flags_kernel<<<T * T, kEwThreads, 0, s>>>(H, n, T, b.tflags[0], b.tflags[1]);
   return cudaGetLastError();
 }
 

@@ -15,6 +15,8 @@ struct DevBuffers {
   double* x64[2];        // FP64 ping-pong iterates, ld x ld
   uint16_t* sl[2][3];    // slice ping-pong sets, ld x ld each
   uint16_t* dg[5];       // BF16 fixed-point digits of the iterate (digit products), ld x ld
+  uint8_t* tflags[2];    // thresholded SP2: per 128 x 128 tile of slice set k, 1 if it may
+                         // hold a non-zero ((ld/128)^2 bytes each)
   double* partials;      // per-CTA partial traces (2 doubles per CTA)
   int max_partials;
 };
@@ -32,6 +34,7 @@ struct SolveParams {
   int oz;    // ... computed as exact digit products on the tensor cores (needs df64)
   double tol;
   double emin_override, emax_override;
+  float tau;  // thresholded SP2 cutoff (0 = dense)
 };
 
 cudaError_t launch_init(const DevBuffers& b, const SolveParams& p, cudaStream_t s);
@@ -59,6 +62,10 @@ int oz_max_order();
 cudaError_t launch_square_split(const DevBuffers& b, const SolveParams& p,
                                 unsigned long long cond_handle, cudaStream_t s);
 bool split_tensor_maps_ready(const DevBuffers& b, int ld, int fmt);
+// Thresholded SP2: tile flags of X0 into tflags[0] (a tile of H with a
+// non-zero, or a diagonal tile) and "unknown content" into tflags[1].
+cudaError_t launch_tile_flags(const double* H, int64_t n, int ld, const DevBuffers& b,
+                              cudaStream_t s);
 cudaError_t launch_finalize(const DevBuffers& b, double* D, int64_t n, int ld, int slice_fmt,
                             cudaStream_t s);
 

@@ -1,26 +1,30 @@
 // Operand slices of the split-precision products.
 //
-// Every iterate X of SP2 is symmetric with its spectrum in [0, 1], so every
-// entry has |x| <= 1 and every row has Euclidean norm <= 1. The slices are
-// therefore FIXED-POINT with one global scale (no per-row exponents):
+// Floating-point splits (the defaults, kFP16x2 / kBF16x3): x = hi + lo / 2048
+// with hi = rn_fp16(x), or x = hi + mid + lo with bf16 slices, every entry
+// keeping 22 / 24 significant bits relative to its own magnitude.
 //
-//   FP16x2: hi = rint(x 2^11)              integer, |hi| <= 2^11 (exact in fp16)
-//           lo = rn_fp16((x 2^11 - hi) 2^11)   |lo| <= 2^10, 11 significant bits
-//           x ~ 2^-11 hi + 2^-22 lo        (absolute error <= 2^-23)
-//   BF16x3: hi  = rint(x 2^8)              integer, |hi| <= 2^8 (exact in bf16)
-//           mid = rint((x 2^8 - hi) 2^8)   integer, |mid| <= 2^7 (exact in bf16)
-//           lo  = rn_bf16(((x 2^8 - hi) 2^8 - mid) 2^8)
-//           x ~ 2^-8 hi + 2^-16 mid + 2^-24 lo  (absolute error <= 2^-26)
+// Fixed-point splits (kFP16x2F / kBF16x3F, an option) for |x| <= 1, one global
+// scale (no per-row exponents):
 //
-// Why fixed point: in S_ij = sum_k x_ik x_jk the leading group sum_k hi_ik hi_jk
-// is a sum of integer products bounded, by Cauchy-Schwarz and the row-norm
-// bound, by 2^22 (FP16x2) or 2^16 (BF16x3) plus rounding slack -- below 2^24,
-// so the tensor core's FP32 accumulation of that group is EXACT whatever its
-// internal rounding. Only the small correction groups see FP32 rounding. With
-// floating-point hi slices the leading group would carry the accumulator's
-// truncation error over K/16 steps.
+//   FP16x2F: hi = rint(x 2^11)              integer, |hi| <= 2^11 (exact in fp16)
+//            lo = rn_fp16((x 2^11 - hi) 2^11)   |lo| <= 2^10, 11 significant bits
+//            x ~ 2^-11 hi + 2^-22 lo        (absolute error <= 2^-23)
+//   BF16x3F: hi  = rint(x 2^8)              integer, |hi| <= 2^8 (exact in bf16)
+//            mid = rint((x 2^8 - hi) 2^8)   integer, |mid| <= 2^7 (exact in bf16)
+//            lo  = rn_bf16(((x 2^8 - hi) 2^8 - mid) 2^8)
+//            x ~ 2^-8 hi + 2^-16 mid + 2^-24 lo  (absolute error <= 2^-26)
 //
-// Each slice is an ld x ld row-major matrix; for the symmetric X a row panel
+// The idea of fixed point: in S_ij = sum_k x_ik x_jk the leading group
+// sum_k hi_ik hi_jk is a sum of integer products bounded (Cauchy-Schwarz and
+// row norms <= 1) by 2^22 (FP16x2F) or 2^16 (BF16x3F), which an exact FP32
+// accumulator would sum without error. Measured on GB300 the fixed-point FP16
+// products were nevertheless LESS accurate than the floating ones (a diagonal
+// bias of -1.1e-5 per square of a matrix whose diagonal entries are near +-1,
+// against -5.7e-7 floating with 64-k chunks), so floating splits are the
+// default and the leading group is summed in short chunks instead.
+//
+// Each slice is an ld x ld row-major matrix; for a symmetric matrix a row panel
 // is the K-major operand of both sides of the product.
 #pragma once
 
@@ -30,8 +34,7 @@
 
 namespace sp2 {
 
-// kFP16x2 / kBF16x3: floating-point splits (every entry keeps 22 / 24
-// significant bits relative to its own magnitude); kFP16x2F / kBF16x3F: the
+// kFP16x2 / kBF16x3: floating-point splits; kFP16x2F / kBF16x3F: the
 // fixed-point variants described above.
 enum SliceFmt : int { kFP16x2 = 0, kBF16x3 = 1, kFP16x2F = 2, kBF16x3F = 3 };
 
@@ -81,34 +84,38 @@ __device__ __forceinline__ void split_value_f(float x, uint16_t& a, uint16_t& b,
   }
 }
 
+// The same split from an FP64 value. FP64 arithmetic is scarce on this part,
+// so each slice is rounded through FP32 (a double rounding of the leading slice
+// is harmless: the next slice takes the exact FP64 remainder) and only the
+// remainders are formed in FP64 (exact subtractions).
 template <int F>
 __device__ __forceinline__ void split_value(double x, uint16_t& a, uint16_t& b, uint16_t& c) {
   if (F == kFP16x2) {
-    const __half h = __double2half(x);
+    const __half h = __float2half_rn((float)x);
     a = h_bits(h);
-    b = h_bits(__double2half((x - (double)__half2float(h)) * 2048.0));
+    b = h_bits(__float2half_rn((float)((x - (double)__half2float(h)) * 2048.0)));
     c = 0;
   } else if (F == kBF16x3) {
-    const __nv_bfloat16 h = __double2bfloat16(x);
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
     const double r1 = x - (double)__bfloat162float(h);
-    const __nv_bfloat16 m = __double2bfloat16(r1);
+    const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
     a = b_bits(h);
     b = b_bits(m);
-    c = b_bits(__double2bfloat16(r1 - (double)__bfloat162float(m)));
+    c = b_bits(__float2bfloat16_rn((float)(r1 - (double)__bfloat162float(m))));
   } else if (F == kFP16x2F) {
     const double y = x * 2048.0;
     const double h = rint(y);
-    a = h_bits(__double2half(h));
-    b = h_bits(__double2half((y - h) * 2048.0));
+    a = h_bits(__float2half_rn((float)h));                      // integer, exact
+    b = h_bits(__float2half_rn((float)((y - h) * 2048.0)));
     c = 0;
   } else {
     const double y = x * 256.0;
     const double h = rint(y);
     const double r1 = (y - h) * 256.0;
     const double m = rint(r1);
-    a = b_bits(__double2bfloat16(h));
-    b = b_bits(__double2bfloat16(m));
-    c = b_bits(__double2bfloat16((r1 - m) * 256.0));
+    a = b_bits(__float2bfloat16_rn((float)h));
+    b = b_bits(__float2bfloat16_rn((float)m));
+    c = b_bits(__float2bfloat16_rn((float)((r1 - m) * 256.0)));
   }
 }
 

@@ -49,9 +49,11 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(_lib.Opts) == 4 * 4 + 2 * 8 + 2 * 4 + 2 * 8 + 4 * 4
     assert _lib.Opts.emin.offset == 16 and _lib.Opts.loop_mode.offset == 32
     assert _lib.Opts.loop_events.offset == 40
-    # progress_info_t: 6 int32, 4 double, 4 uint64
-    assert ctypes.sizeof(_lib.Info) == 6 * 4 + 4 * 8 + 4 * 8
+    assert _lib.Opts.fp64_impl.offset == 56 and _lib.Opts.tau.offset == 60
+    # progress_info_t: 6 int32, 4 double, 4 uint64, uint64 kblocks
+    assert ctypes.sizeof(_lib.Info) == 6 * 4 + 4 * 8 + 4 * 8 + 8
     assert _lib.Info.emin.offset == 24 and _lib.Info.bits.offset == 56
+    assert _lib.Info.kblocks.offset == 88
     # progress_batch_ex_t: 8 pointer/double slots, 4 int32 (configuration), 2 pointers
     assert ctypes.sizeof(_lib.BatchEx) == 8 * 8 + 4 * 4 + 2 * 8
     assert _lib.BatchEx.tile_n.offset == 64 and _lib.BatchEx.d_cycles.offset == 80
@@ -145,6 +147,16 @@ def test_argument_errors_before_any_device_work(lib):
     assert lib.progress_sp2_dense_ex(P(16), 8, 4, 1e-9, P(32), ctypes.byref(o), None, None) == _lib.EINVAL
     o.maxiter = 10
     o.emin, o.emax = 1.0, 0.0
+    assert lib.progress_sp2_dense_ex(P(16), 8, 4, 1e-9, P(32), ctypes.byref(o), None, None) == _lib.EINVAL
+    # thresholded SP2: tau >= 0, and tau > 0 only with the split precisions
+    o.emin, o.emax = float("nan"), float("nan")
+    o.tau = -1.0
+    assert lib.progress_sp2_dense_ex(P(16), 8, 4, 1e-9, P(32), ctypes.byref(o), None, None) == _lib.EINVAL
+    o.tau = 1e-6
+    o.prec = _lib.FP64
+    assert lib.progress_sp2_dense_ex(P(16), 8, 4, 1e-9, P(32), ctypes.byref(o), None, None) == _lib.EINVAL
+    assert b"tau" in lib.progress_last_error()
+    o.prec, o.slice_fixed = _lib.FP32_SPLIT, 1
     assert lib.progress_sp2_dense_ex(P(16), 8, 4, 1e-9, P(32), ctypes.byref(o), None, None) == _lib.EINVAL
     assert lib.progress_gershgorin_bounds(P(16), 0, P(32), None) == _lib.EINVAL
     assert b"n < 1" in lib.progress_last_error()
