@@ -789,7 +789,7 @@ def run_sparse(args):
     H = torch.from_numpy(H_np).to(dev)
     D = torch.empty_like(H)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    opts = dict(prec="fp32_split", tau=tau)
+    opts = dict(prec="fp32_split", tau=tau, loop_mode=args.loop_mode)
     info = None
     for _ in range(max(1, args.warmup)):
         D, info = pkg.sp2_dense_ex(H, nocc, 1e-9, D=D, **opts)
