@@ -37,12 +37,12 @@
 //                      Tr X', ||X'||_F^2 (FP32 over 32 columns, folded into
 //                      FP64 per chunk).
 //
-// Thresholded SP2 (template flag SP; Listing 1's cutoff tau): the epilogue
-// drops |x| < tau from the product and from 2X - X^2 and records, per 128 x 128
-// tile, whether the new iterate holds a non-zero there (tflags, one byte per
-// tile and slice set). A tile (I, J) then streams only the k-blocks whose tiles
-// (I, k) and (J, k) of X may be non-zero, and a result tile with no product
-// term that the destination set already holds as zeros is not written.
+// Thresholded SP2 (Listing 1's cutoff tau) has its own persistent kernel below,
+// square_split_sparse_kernel: the epilogue drops |x| < tau from the product and
+// from 2X - X^2 and records, per 128 x 128 tile, whether the new iterate holds a
+// non-zero there (tflags, one byte per tile and slice set); a tile (I, J) then
+// streams only the k-blocks whose tiles (I, k) and (J, k) of X may be non-zero,
+// and a result tile that stays zero where zeros already are is skipped.
 //
 // Every mbarrier wait is bounded; a wait that runs out records
 // PROGRESS_ETIMEOUT in the solve state, stops the loop and the CTA still frees
@@ -89,10 +89,10 @@ struct TensorMaps {
 
 using namespace tc;
 
-template <int F, bool SP>
+template <int F>
 __global__ void __launch_bounds__(THREADS, 1)
     square_split_kernel(const __grid_constant__ TensorMaps maps, DevBuffers buf,
-                        unsigned long long cond, float tau) {
+                        unsigned long long cond) {
   using C = Cfg<F>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint32_t s_tmem;
@@ -100,10 +100,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   __shared__ int s_consumed;
   __shared__ int s_last;
   __shared__ double s_scratch[2 * THREADS / 32];
-  // thresholded SP2: the k-blocks (64 wide) whose 128-wide tiles of both row
-  // panels may hold non-zeros, in increasing order
-  __shared__ uint16_t s_klist[SP ? 1024 : 1];
-  __shared__ int s_wcnt[THREADS / 32];
 
   State* st = buf.st;
   const int done = __ldcg(&st->done);
@@ -139,44 +135,372 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t chunk_full = bars + 8u * (2 * C::STAGES + 1);              // [NBUF]
   const uint32_t chunk_empty = bars + 8u * (2 * C::STAGES + 1 + C::NBUF);   // [NBUF]
 
-  const int KB = ld / BK;
-  // SP: list of the active k-blocks (every thread counts them the same way)
-  int nkb = KB;
-  bool tile_was_zero = false;  // SP: this tile of the destination set holds zeros
-  bool x_tile_zero = false;    // SP: this tile of X is zero
-  if (SP) {
-    const uint8_t* fl = buf.tflags[src];
-    int total = 0;
-    for (int base = 0; base < T; base += THREADS) {
-      const int t = base + (int)threadIdx.x;
-      const bool act = t < T && fl[(size_t)I * T + t] != 0 && fl[(size_t)J * T + t] != 0;
-      const unsigned bal = __ballot_sync(0xffffffffu, act);
-      if (lane == 0) s_wcnt[warp] = __popc(bal);
-      __syncthreads();
-      int before = total, sum = 0;
-      for (int w2 = 0; w2 < THREADS / 32; ++w2) {
-        if (w2 < warp) before += s_wcnt[w2];
-        sum += s_wcnt[w2];
-      }
-      before += __popc(bal & ((1u << lane) - 1u));
-      if (act) {
-        s_klist[2 * before] = (uint16_t)(2 * t);
-        s_klist[2 * before + 1] = (uint16_t)(2 * t + 1);
-      }
-      total += sum;
-      __syncthreads();
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    s_consumed = 0;
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
     }
-    nkb = 2 * total;
-    if (threadIdx.x == 0 && nkb > 0) atomicAdd(&st->kblocks, (unsigned long long)nkb);
-    tile_was_zero = buf.tflags[dst][(size_t)I * T + J] == 0;
-    x_tile_zero = fl[(size_t)I * T + J] == 0;
+    mbar_init(accum_bar, 1);
+    for (int b = 0; b < C::NBUF; ++b) {
+      mbar_init(chunk_full + 8u * b, 1);
+      mbar_init(chunk_empty + 8u * b, DRAIN_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
-  // SP: a result tile with no product term is 0 (X^2) or prune(2X) = 0 (X zero
-  // there); if the destination already holds zeros there is nothing to do but
-  // to report zero traces (no tensor memory, no barriers, no stores)
-  const bool skip_cta = SP && nkb == 0 && (bit == 0 || x_tile_zero) && tile_was_zero;
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  volatile int* err = &s_err;
+
+  const int KB = ld / BK;
+  const int NC = (KB + CHUNK - 1) / CHUNK;  // leading-group chunks
+  int issued = 0;  // k-blocks whose loads were issued (producer thread)
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer
+      for (int kb = 0; kb < KB; ++kb, ++issued) {
+        const int s = kb % C::STAGES;
+        const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+        if (!mbar_wait(empty_bar(s), ph ^ 1u, err)) break;
+        mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
+        const uint32_t sa = base + s * C::STAGE_BYTES;
+#pragma unroll
+        for (int j = 0; j < C::NS; ++j) {
+          tma_load_2d(sa + j * TILE_BYTES, &maps.m[src][j], kb * BK, row_a, full_bar(s));
+          tma_load_2d(sa + (C::NS + j) * TILE_BYTES, &maps.m[src][j], kb * BK, row_b,
+                      full_bar(s));
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer. The leading group goes to one of two chunk accumulators
+      // (CHUNK k-blocks each) that the drain warps empty in turn; the
+      // correction groups accumulate over the whole K.
+      constexpr uint32_t idesc = idesc_f16(fmt_bf16(F) ? 1 : 0, BM, BN);
+      const uint32_t acc1 = tmem + 128u * C::NBUF, acc2 = acc1 + 128u;
+      bool ok = true;
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        const int c = kb / CHUNK, cb = c % C::NBUF;
+        const bool chunk_first = (kb % CHUNK) == 0;
+        const bool chunk_last = (kb % CHUNK) == CHUNK - 1 || kb == KB - 1;
+        const uint32_t acc0 = tmem + 128u * cb;
+        if (chunk_first) {
+          if (!mbar_wait(chunk_empty + 8u * cb, ((uint32_t)(c / C::NBUF) & 1u) ^ 1u, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
+        const int s = kb % C::STAGES;
+        const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+        if (!mbar_wait(full_bar(s), ph, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = base + s * C::STAGE_BYTES;
+        uint64_t a[3], b[3];
+#pragma unroll
+        for (int j = 0; j < C::NS; ++j) {
+          a[j] = smem_desc_sw128(sa + j * TILE_BYTES);
+          b[j] = smem_desc_sw128(sa + (C::NS + j) * TILE_BYTES);
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 32 B per K = 16 step
+          const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+          const uint32_t chunk_acc = (chunk_first && kk == 0) ? 0u : 1u;
+          mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, chunk_acc);
+          mma_f16(acc1, a[0] + adv, b[1] + adv, idesc, first);
+          mma_f16(acc1, a[1] + adv, b[0] + adv, idesc, 1u);
+          if (fmt_bf16(F)) {
+            mma_f16(acc2, a[0] + adv, b[2] + adv, idesc, first);
+            mma_f16(acc2, a[2] + adv, b[0] + adv, idesc, 1u);
+            mma_f16(acc2, a[1] + adv, b[1] + adv, idesc, 1u);
+          }
+        }
+        mma_commit(empty_bar(s));  // frees the stage once these MMAs have read it
+        if (chunk_last) mma_commit(chunk_full + 8u * cb);
+        s_consumed = kb + 1;
+      }
+      mma_commit(accum_bar);  // all MMAs issued so far are complete -> epilogue
+    }
+    __syncwarp();
+  }
+
+  // ---- drain warps: thread owns TMEM lane = tile row and DCOLS columns, sums
+  // the leading-group chunks with round-to-nearest FP32 adds, then runs the
+  // epilogue.
+  const bool drain = warp >= DRAIN_WARP0;
+  const int quarter = warp & 3;
+  const int half = drain ? (warp - DRAIN_WARP0) >> 2 : 0;
+  const int row = quarter * 32 + lane;
+  const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+  float sum0[DCOLS];
+#pragma unroll
+  for (int j = 0; j < DCOLS; ++j) sum0[j] = 0.0f;
+  if (drain) {
+    for (int c = 0; c < NC; ++c) {
+      const int cb = c % C::NBUF;
+      if (!mbar_wait(chunk_full + 8u * cb, (uint32_t)(c / C::NBUF) & 1u, err)) break;
+      tc_fence_after();
+      float v[DCOLS];
+#pragma unroll
+      for (int q = 0; q < DCOLS / 32; ++q) tmem_ld32(lane_addr + 128u * cb + half * DCOLS + q * 32, v + q * 32);
+      tmem_ld_wait();
+      // the values are in registers: free the buffer before adding them
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(chunk_empty + 8u * cb)
+                     : "memory");
+#pragma unroll
+      for (int j = 0; j < DCOLS; ++j) sum0[j] += v[j];
+    }
+  }
+  // (the MMA thread always commits accum_bar, so this wait does not abort
+  // early: no MMA may still be writing tensor memory past it)
+  const bool ok = mbar_wait(accum_bar, 0u, err, false);
+  tc_fence_after();
   double tr = 0.0, fr = 0.0;
-  if (!skip_cta) {
+  if (drain && ok && *err == 0) {
+    using W = SliceWeights<F>;
+    const int r = row_a + row;
+    // (selects, not a runtime index into the parameter arrays)
+    const bool odd = src != 0;
+    const uint16_t* xs0 = odd ? buf.sl[1][0] : buf.sl[0][0];
+    const uint16_t* xs1 = odd ? buf.sl[1][1] : buf.sl[0][1];
+    const uint16_t* xs2 = odd ? buf.sl[1][2] : buf.sl[0][2];
+    uint16_t* const out0 = odd ? buf.sl[0][0] : buf.sl[1][0];
+    uint16_t* const out1 = odd ? buf.sl[0][1] : buf.sl[1][1];
+    uint16_t* const out2 = odd ? buf.sl[0][2] : buf.sl[1][2];
+    double* out64 = odd ? buf.x64[0] : buf.x64[1];
+    // FP64-accurate phases read the next iterate from the FP64 buffer: as
+    // doubles, or as double-float planes (hi = x, lo = 0)
+    const bool df = st->df64 != 0;
+    float* out_hi = reinterpret_cast<float*>(out64);
+    float* out_lo = out_hi + (size_t)ld * ld;
+    // staging of the (r, c) slice stores in the idle operand ring: per warp
+    // 32 rows x 32 columns of packed (slice0 | slice1 << 16) words (row
+    // stride 33) and, for BF16x3, of slice-2 half words (row stride 34)
+    uint32_t* stA = reinterpret_cast<uint32_t*>(smem_raw + (base - smem_u32(smem_raw))) +
+                    (warp - DRAIN_WARP0) * (32 * 33);
+    uint16_t* stB = reinterpret_cast<uint16_t*>(smem_raw + (base - smem_u32(smem_raw)) +
+                                                DRAIN_WARPS * 32 * 33 * 4) +
+                    (warp - DRAIN_WARP0) * (32 * 34);
+    const int rb = row_a + quarter * 32;
+#pragma unroll
+    for (int ch = 0; ch < DCOLS / 32; ++ch) {
+      const int col = half * DCOLS + ch * 32;  // column in the tile
+      const int c0 = row_b + col;
+      float trf = 0.0f, frf = 0.0f;  // chunk partials (FP32), folded into FP64 below
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int cs = c0 + hh * 16;
+        // the mirror values of X for 2X - X^2 do not depend on the products:
+        // load them before waiting on tensor memory (packed slice0 | slice1)
+        uint32_t m01[16], m2[16];
+        if (bit) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const size_t m = (size_t)(cs + j) * ld + r;  // X is symmetric: coalesced
+            m01[j] = (uint32_t)xs0[m] | ((uint32_t)xs1[m] << 16);
+            m2[j] = fmt_bf16(F) ? (uint32_t)xs2[m] : 0u;
+          }
+        }
+        uint32_t u1[16], u2[16];
+        tmem_ld16(lane_addr + 128u * C::NBUF + col + hh * 16, u1);
+        if (fmt_bf16(F)) tmem_ld16(lane_addr + 128u * (C::NBUF + 1) + col + hh * 16, u2);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int jj = hh * 16 + j;  // column within the 32-column chunk
+          const int c = cs + j;
+          float x = sum0[ch * 32 + jj] * W::w0 + __uint_as_float(u1[j]) * W::w1;
+          if (fmt_bf16(F)) x += __uint_as_float(u2[j]) * W::w2;
+          if (bit)
+            x = 2.0f * join_value<F>((uint16_t)(m01[j] & 0xffffu), (uint16_t)(m01[j] >> 16),
+                                     (uint16_t)m2[j]) -
+                x;
+          uint16_t a, b2, c2;
+          split_value_f<F>(x, a, b2, c2);
+          stA[lane * 33 + jj] = (uint32_t)a | ((uint32_t)b2 << 16);
+          if (fmt_bf16(F)) stB[lane * 34 + jj] = c2;
+          if (r <= c) {
+            if (r == c) {
+              trf += x;
+              frf += x * x;
+            } else {
+              frf += 2.0f * x * x;
+              // mirror (c, r): consecutive threads write consecutive r
+              const size_t m = (size_t)c * ld + r;
+              out0[m] = a;
+              out1[m] = b2;
+              if (fmt_bf16(F)) out2[m] = c2;
+              if (want_fp64) {
+                if (df) {
+                  out_hi[m] = x;
+                  out_lo[m] = 0.0f;
+                } else {
+                  out64[m] = (double)x;
+                }
+              }
+            }
+            if (want_fp64) {  // (r, c), a few products per solve: direct stores
+              const size_t d = (size_t)r * ld + c;
+              if (df) {
+                out_hi[d] = x;
+                out_lo[d] = 0.0f;
+              } else {
+                out64[d] = (double)x;
+              }
+            }
+          }
+        }
+      }
+      tr += (double)trf;
+      fr += (double)frf;
+      // (r, c) slices: 32 rows of 32 columns back out, one row per store
+      __syncwarp();
+      const int cc = c0 + lane;
+#pragma unroll 4
+      for (int i = 0; i < 32; ++i) {
+        if (rb + i <= cc) {
+          const uint32_t v = stA[i * 33 + lane];
+          const size_t d = (size_t)(rb + i) * ld + cc;
+          out0[d] = (uint16_t)(v & 0xffffu);
+          out1[d] = (uint16_t)(v >> 16);
+          if (fmt_bf16(F)) out2[d] = stB[i * 34 + lane];
+        }
+      }
+      __syncwarp();
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*err) {
+    // failure path: let TMA copies still in flight land before the CTA exits
+    if (threadIdx.x == 0) {
+      for (int kb = s_consumed; kb < issued; ++kb)
+        mbar_wait(full_bar(kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, err, false,
+                  kWaitLimitNs / 10);
+    }
+    __syncthreads();
+  }
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+  if (*err && threadIdx.x == 0) {
+    st->status = PROGRESS_ETIMEOUT;
+    st->done = 1;
+  }
+
+  block_sum2(tr, fr, s_scratch);
+  if (threadIdx.x == 0) {
+    buf.partials[2 * blockIdx.x] = tr;
+    buf.partials[2 * blockIdx.x + 1] = fr;
+  }
+  if (!last_cta_arrives(st, gridDim.x, &s_last)) return;
+  double a, b;
+  reduce_partials(buf.partials, gridDim.x, a, b, s_scratch);
+  if (threadIdx.x == 0) {
+    st->ticket = 0u;
+    if (st->status == PROGRESS_ETIMEOUT) {
+      st->done = 1;
+    } else {
+      st->t1 = a;
+      st->t2 = b;
+      st->iter = k_iter + 1;
+      st->phase_iters[kPhaseSplit] += 1;
+      st->x_fp64_valid = want_fp64 ? 1 : 0;
+      st->x_slices_valid = 1;
+      decide(st);
+    }
+    if (st->done && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+  }
+}
+
+// Thresholded SP2 product (Listing 1's cutoff tau), persistent: one CTA per SM
+// walks the upper tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... First every
+// warp checks one tile at a time (all warps at once): a tile needs work unless
+// no k-tile pair (I, k), (J, k) of X is flagged non-zero, the result is zero
+// (X^2, or X zero there) and the destination set already holds zeros there.
+// The tiles that need work then run the pipeline of square_split_kernel one
+// after the other with tensor memory and mbarriers kept across tiles (the
+// stage, chunk and accumulator phases continue from tile to tile), streaming
+// only the flagged k-blocks. The epilogue prunes |x| < tau from the product and
+// from 2X - X^2 and writes the tile's new flag.
+constexpr int SP_MAX_TILES = 1024;  // tiles per CTA (the host sizes the grid)
+
+template <int F>
+__global__ void __launch_bounds__(THREADS, 1)
+    square_split_sparse_kernel(const __grid_constant__ TensorMaps maps, DevBuffers buf,
+                               unsigned long long cond, float tau) {
+  using C = Cfg<F>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_err;
+  __shared__ int s_consumed;  // global k-block index consumed by the MMA thread
+  __shared__ int s_last;
+  __shared__ double s_scratch[2 * THREADS / 32];
+  __shared__ uint16_t s_klist[1024];
+  __shared__ int s_wcnt[THREADS / 32];
+  __shared__ uint8_t s_work[SP_MAX_TILES];
+
+  State* st = buf.st;
+  const int done = __ldcg(&st->done);
+  const int phase = __ldcg(&st->phase);
+  if (done) {
+    if (cond && blockIdx.x == 0 && threadIdx.x == 0)
+      cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+    return;
+  }
+  if (phase != kPhaseSplit) return;
+  const int k_iter = __ldcg(&st->iter);
+  const int bit = __ldcg(&st->bit);
+  const int ld = st->ld;
+  const int src = k_iter & 1, dst = (k_iter + 1) & 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int T = ld / BM;
+  const int tiles = T * (T + 1) / 2;
+  const int my_tiles = (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const uint8_t* fl = buf.tflags[src];
+  uint8_t* fd = buf.tflags[dst];
+
+  // pass 1: which of this CTA's tiles need work (one warp per tile)
+  for (int j = warp; j < my_tiles; j += THREADS / 32) {
+    int I, J;
+    tri_tile((int)blockIdx.x + j * (int)gridDim.x, T, I, J);
+    bool any = false;
+    for (int b0 = 0; b0 < T && !any; b0 += 32) {
+      const int q = b0 + lane;
+      any = __any_sync(0xffffffffu, q < T && fl[(size_t)I * T + q] != 0 &&
+                                        fl[(size_t)J * T + q] != 0);
+    }
+    if (lane == 0) {
+      const bool zero_result = !any && (bit == 0 || fl[(size_t)I * T + J] == 0);
+      s_work[j] = (zero_result && fd[(size_t)I * T + J] == 0) ? 0 : 1;
+    }
+  }
+  __syncthreads();
+  int nwork = 0;
+  for (int j = 0; j < my_tiles; ++j) nwork += s_work[j];
+
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t bars = base + C::STAGES * C::STAGE_BYTES;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (C::STAGES + s); };
+  const uint32_t accum_bar = bars + 8u * (2 * C::STAGES);
+  const uint32_t chunk_full = bars + 8u * (2 * C::STAGES + 1);
+  const uint32_t chunk_empty = bars + 8u * (2 * C::STAGES + 1 + C::NBUF);
+
+  double tr = 0.0, fr = 0.0;
+  if (nwork > 0) {
     if (threadIdx.x == 0) {
       s_err = 0;
       s_consumed = 0;
@@ -198,261 +522,258 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     volatile int* err = &s_err;
-
-    const int NC = (nkb + CHUNK - 1) / CHUNK;  // leading-group chunks
-    int issued = 0;  // k-blocks whose loads were issued (producer thread)
-    if (warp == 0) {
-      if (lane == 0) {
-        // TMA producer
-        for (int q = 0; q < nkb; ++q, ++issued) {
-          const int kb = SP ? (int)s_klist[q] : q;
-          const int s = q % C::STAGES;
-          const uint32_t ph = (uint32_t)(q / C::STAGES) & 1u;
-          if (!mbar_wait(empty_bar(s), ph ^ 1u, err)) break;
-          mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
-          const uint32_t sa = base + s * C::STAGE_BYTES;
-#pragma unroll
-          for (int j = 0; j < C::NS; ++j) {
-            tma_load_2d(sa + j * TILE_BYTES, &maps.m[src][j], kb * BK, row_a, full_bar(s));
-            tma_load_2d(sa + (C::NS + j) * TILE_BYTES, &maps.m[src][j], kb * BK, row_b,
-                        full_bar(s));
-          }
-        }
-      }
-      __syncwarp();
-    } else if (warp == 1) {
-      if (lane == 0) {
-        // MMA issuer. The leading group goes to one of two chunk accumulators
-        // (CHUNK k-blocks each) that the drain warps empty in turn; the
-        // correction groups accumulate over the whole K.
-        constexpr uint32_t idesc = idesc_f16(fmt_bf16(F) ? 1 : 0, BM, BN);
-        const uint32_t acc1 = tmem + 128u * C::NBUF, acc2 = acc1 + 128u;
-        bool ok = true;
-        for (int q = 0; q < nkb && ok; ++q) {
-          const int c = q / CHUNK, cb = c % C::NBUF;
-          const bool chunk_first = (q % CHUNK) == 0;
-          const bool chunk_last = (q % CHUNK) == CHUNK - 1 || q == nkb - 1;
-          const uint32_t acc0 = tmem + 128u * cb;
-          if (chunk_first) {
-            if (!mbar_wait(chunk_empty + 8u * cb, ((uint32_t)(c / C::NBUF) & 1u) ^ 1u, err)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-          }
-          const int s = q % C::STAGES;
-          const uint32_t ph = (uint32_t)(q / C::STAGES) & 1u;
-          if (!mbar_wait(full_bar(s), ph, err)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t sa = base + s * C::STAGE_BYTES;
-          uint64_t a[3], b[3];
-#pragma unroll
-          for (int j = 0; j < C::NS; ++j) {
-            a[j] = smem_desc_sw128(sa + j * TILE_BYTES);
-            b[j] = smem_desc_sw128(sa + (C::NS + j) * TILE_BYTES);
-          }
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 32 B per K = 16 step
-            const uint32_t first = (q == 0 && kk == 0) ? 0u : 1u;
-            const uint32_t chunk_acc = (chunk_first && kk == 0) ? 0u : 1u;
-            mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, chunk_acc);
-            mma_f16(acc1, a[0] + adv, b[1] + adv, idesc, first);
-            mma_f16(acc1, a[1] + adv, b[0] + adv, idesc, 1u);
-            if (fmt_bf16(F)) {
-              mma_f16(acc2, a[0] + adv, b[2] + adv, idesc, first);
-              mma_f16(acc2, a[2] + adv, b[0] + adv, idesc, 1u);
-              mma_f16(acc2, a[1] + adv, b[1] + adv, idesc, 1u);
-            }
-          }
-          mma_commit(empty_bar(s));  // frees the stage once these MMAs have read it
-          if (chunk_last) mma_commit(chunk_full + 8u * cb);
-          s_consumed = q + 1;
-        }
-        if (nkb > 0)
-          mma_commit(accum_bar);  // all MMAs issued so far are complete -> epilogue
-        else  // SP: no product term at all
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(accum_bar) : "memory");
-      }
-      __syncwarp();
-    }
-
-    // ---- drain warps: thread owns TMEM lane = tile row and DCOLS columns, sums
-    // the leading-group chunks with round-to-nearest FP32 adds, then runs the
-    // epilogue.
     const bool drain = warp >= DRAIN_WARP0;
     const int quarter = warp & 3;
     const int half = drain ? (warp - DRAIN_WARP0) >> 2 : 0;
     const int row = quarter * 32 + lane;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-    float sum0[DCOLS];
-#pragma unroll
-    for (int j = 0; j < DCOLS; ++j) sum0[j] = 0.0f;
-    if (drain) {
-      for (int c = 0; c < NC; ++c) {
-        const int cb = c % C::NBUF;
-        if (!mbar_wait(chunk_full + 8u * cb, (uint32_t)(c / C::NBUF) & 1u, err)) break;
-        tc_fence_after();
-        float v[DCOLS];
-#pragma unroll
-        for (int q = 0; q < DCOLS / 32; ++q) tmem_ld32(lane_addr + 128u * cb + half * DCOLS + q * 32, v + q * 32);
-        tmem_ld_wait();
-        // the values are in registers: free the buffer before adding them
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0)
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(chunk_empty + 8u * cb)
-                       : "memory");
-#pragma unroll
-        for (int j = 0; j < DCOLS; ++j) sum0[j] += v[j];
+    const bool odd = src != 0;
+    const uint16_t* xs0 = odd ? buf.sl[1][0] : buf.sl[0][0];
+    const uint16_t* xs1 = odd ? buf.sl[1][1] : buf.sl[0][1];
+    const uint16_t* xs2 = odd ? buf.sl[1][2] : buf.sl[0][2];
+    uint16_t* const out0 = odd ? buf.sl[0][0] : buf.sl[1][0];
+    uint16_t* const out1 = odd ? buf.sl[0][1] : buf.sl[1][1];
+    uint16_t* const out2 = odd ? buf.sl[0][2] : buf.sl[1][2];
+    int g = 0;        // k-blocks of the earlier tiles (stage ring position)
+    int gc = 0;       // leading-group chunks of the earlier tiles
+    int ntile = 0;    // tiles done (accumulator barrier phase)
+    int issued = 0;   // producer: global k-blocks whose loads were issued
+    for (int j = 0; j < my_tiles; ++j) {
+      if (!s_work[j]) continue;
+      int I, J;
+      tri_tile((int)blockIdx.x + j * (int)gridDim.x, T, I, J);
+      const int row_a = I * BM, row_b = J * BN;
+      // this tile's flagged k-blocks, in order (every thread counts the same)
+      int total = 0;
+      for (int b0 = 0; b0 < T; b0 += THREADS) {
+        const int t = b0 + (int)threadIdx.x;
+        const bool act = t < T && fl[(size_t)I * T + t] != 0 && fl[(size_t)J * T + t] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = total, sum = 0;
+        for (int w2 = 0; w2 < THREADS / 32; ++w2) {
+          if (w2 < warp) before += s_wcnt[w2];
+          sum += s_wcnt[w2];
+        }
+        before += __popc(bal & ((1u << lane) - 1u));
+        if (act) {
+          s_klist[2 * before] = (uint16_t)(2 * t);
+          s_klist[2 * before + 1] = (uint16_t)(2 * t + 1);
+        }
+        total += sum;
+        __syncthreads();
       }
-    }
-    // (the MMA thread always commits accum_bar, so this wait does not abort
-    // early: no MMA may still be writing tensor memory past it)
-    const bool ok = mbar_wait(accum_bar, 0u, err, false);
-    tc_fence_after();
-    int nz = 0;  // SP: this thread wrote a non-zero
-    if (drain && ok && *err == 0) {
-      using W = SliceWeights<F>;
-      const int r = row_a + row;
-      // (selects, not a runtime index into the parameter arrays)
-      const bool odd = src != 0;
-      const uint16_t* xs0 = odd ? buf.sl[1][0] : buf.sl[0][0];
-      const uint16_t* xs1 = odd ? buf.sl[1][1] : buf.sl[0][1];
-      const uint16_t* xs2 = odd ? buf.sl[1][2] : buf.sl[0][2];
-      uint16_t* const out0 = odd ? buf.sl[0][0] : buf.sl[1][0];
-      uint16_t* const out1 = odd ? buf.sl[0][1] : buf.sl[1][1];
-      uint16_t* const out2 = odd ? buf.sl[0][2] : buf.sl[1][2];
-      double* out64 = odd ? buf.x64[0] : buf.x64[1];
-      // FP64-accurate phases read the next iterate from the FP64 buffer: as
-      // doubles, or as double-float planes (hi = x, lo = 0)
-      const bool df = st->df64 != 0;
-      float* out_hi = reinterpret_cast<float*>(out64);
-      float* out_lo = out_hi + (size_t)ld * ld;
-      // staging of the (r, c) slice stores in the idle operand ring: per warp
-      // 32 rows x 32 columns of packed (slice0 | slice1 << 16) words (row
-      // stride 33) and, for BF16x3, of slice-2 half words (row stride 34)
-      uint32_t* stA = reinterpret_cast<uint32_t*>(smem_raw + (base - smem_u32(smem_raw))) +
-                      (warp - DRAIN_WARP0) * (32 * 33);
-      uint16_t* stB = reinterpret_cast<uint16_t*>(smem_raw + (base - smem_u32(smem_raw)) +
-                                                  DRAIN_WARPS * 32 * 33 * 4) +
-                      (warp - DRAIN_WARP0) * (32 * 34);
-      const int rb = row_a + quarter * 32;
+      const int nkb = 2 * total;
+      const int NC = (nkb + CHUNK - 1) / CHUNK;
+      if (threadIdx.x == 0 && nkb > 0) atomicAdd(&st->kblocks, (unsigned long long)nkb);
+      if (warp == 0) {
+        if (lane == 0) {
+          for (int q = 0; q < nkb; ++q) {
+            const int gq = g + q;
+            const int s = gq % C::STAGES;
+            const uint32_t ph = (uint32_t)(gq / C::STAGES) & 1u;
+            if (!mbar_wait(empty_bar(s), ph ^ 1u, err)) break;
+            mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
+            const uint32_t sa = base + s * C::STAGE_BYTES;
+            const int kb = (int)s_klist[q];
 #pragma unroll
-      for (int ch = 0; ch < DCOLS / 32; ++ch) {
-        const int col = half * DCOLS + ch * 32;  // column in the tile
-        const int c0 = row_b + col;
-        float trf = 0.0f, frf = 0.0f;  // chunk partials (FP32), folded into FP64 below
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const int cs = c0 + hh * 16;
-          // the mirror values of X for 2X - X^2 do not depend on the products:
-          // load them before waiting on tensor memory (packed slice0 | slice1)
-          uint32_t m01[16], m2[16];
-          if (bit) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const size_t m = (size_t)(cs + j) * ld + r;  // X is symmetric: coalesced
-              m01[j] = (uint32_t)xs0[m] | ((uint32_t)xs1[m] << 16);
-              m2[j] = fmt_bf16(F) ? (uint32_t)xs2[m] : 0u;
+            for (int jj = 0; jj < C::NS; ++jj) {
+              tma_load_2d(sa + jj * TILE_BYTES, &maps.m[src][jj], kb * BK, row_a, full_bar(s));
+              tma_load_2d(sa + (C::NS + jj) * TILE_BYTES, &maps.m[src][jj], kb * BK, row_b,
+                          full_bar(s));
             }
+            issued = gq + 1;
           }
-          uint32_t u1[16], u2[16];
-          if (!SP || nkb > 0) {
-            tmem_ld16(lane_addr + 128u * C::NBUF + col + hh * 16, u1);
-            if (fmt_bf16(F)) tmem_ld16(lane_addr + 128u * (C::NBUF + 1) + col + hh * 16, u2);
-            tmem_ld_wait();
-          } else {
+        }
+        __syncwarp();
+      } else if (warp == 1) {
+        if (lane == 0) {
+          constexpr uint32_t idesc = idesc_f16(fmt_bf16(F) ? 1 : 0, BM, BN);
+          const uint32_t acc1 = tmem + 128u * C::NBUF, acc2 = acc1 + 128u;
+          bool ok = true;
+          for (int q = 0; q < nkb && ok; ++q) {
+            const int c = gc + q / CHUNK, cb = c % C::NBUF;
+            const bool chunk_first = (q % CHUNK) == 0;
+            const bool chunk_last = (q % CHUNK) == CHUNK - 1 || q == nkb - 1;
+            const uint32_t acc0 = tmem + 128u * cb;
+            if (chunk_first) {
+              if (!mbar_wait(chunk_empty + 8u * cb, ((uint32_t)(c / C::NBUF) & 1u) ^ 1u, err)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+            }
+            const int gq = g + q;
+            const int s = gq % C::STAGES;
+            const uint32_t ph = (uint32_t)(gq / C::STAGES) & 1u;
+            if (!mbar_wait(full_bar(s), ph, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = base + s * C::STAGE_BYTES;
+            uint64_t a[3], b[3];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) u1[j] = u2[j] = 0u;
+            for (int jj = 0; jj < C::NS; ++jj) {
+              a[jj] = smem_desc_sw128(sa + jj * TILE_BYTES);
+              b[jj] = smem_desc_sw128(sa + (C::NS + jj) * TILE_BYTES);
+            }
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+              const uint32_t first = (q == 0 && kk == 0) ? 0u : 1u;
+              const uint32_t chunk_acc = (chunk_first && kk == 0) ? 0u : 1u;
+              mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, chunk_acc);
+              mma_f16(acc1, a[0] + adv, b[1] + adv, idesc, first);
+              mma_f16(acc1, a[1] + adv, b[0] + adv, idesc, 1u);
+              if (fmt_bf16(F)) {
+                mma_f16(acc2, a[0] + adv, b[2] + adv, idesc, first);
+                mma_f16(acc2, a[2] + adv, b[0] + adv, idesc, 1u);
+                mma_f16(acc2, a[1] + adv, b[1] + adv, idesc, 1u);
+              }
+            }
+            mma_commit(empty_bar(s));
+            if (chunk_last) mma_commit(chunk_full + 8u * cb);
+            s_consumed = gq + 1;
           }
+          if (nkb > 0)
+            mma_commit(accum_bar);
+          else
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(accum_bar) : "memory");
+        }
+        __syncwarp();
+      }
+      float sum0[DCOLS];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int jj = hh * 16 + j;  // column within the 32-column chunk
-            const int c = cs + j;
-            float x = sum0[ch * 32 + jj] * W::w0 + __uint_as_float(u1[j]) * W::w1;
-            if (fmt_bf16(F)) x += __uint_as_float(u2[j]) * W::w2;
-            if (SP && fabsf(x) < tau) x = 0.0f;  // prune the product
+      for (int jj = 0; jj < DCOLS; ++jj) sum0[jj] = 0.0f;
+      if (drain) {
+        for (int c = 0; c < NC; ++c) {
+          const int gcc = gc + c, cb = gcc % C::NBUF;
+          if (!mbar_wait(chunk_full + 8u * cb, (uint32_t)(gcc / C::NBUF) & 1u, err)) break;
+          tc_fence_after();
+          float v[DCOLS];
+#pragma unroll
+          for (int q = 0; q < DCOLS / 32; ++q)
+            tmem_ld32(lane_addr + 128u * cb + half * DCOLS + q * 32, v + q * 32);
+          tmem_ld_wait();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(chunk_empty + 8u * cb)
+                         : "memory");
+#pragma unroll
+          for (int jj = 0; jj < DCOLS; ++jj) sum0[jj] += v[jj];
+        }
+      }
+      const bool ok = mbar_wait(accum_bar, (uint32_t)ntile & 1u, err, false);
+      tc_fence_after();
+      int nz = 0;
+      if (drain && ok && *err == 0) {
+        using W = SliceWeights<F>;
+        const int r = row_a + row;
+        uint32_t* stA = reinterpret_cast<uint32_t*>(smem_raw + (base - smem_u32(smem_raw))) +
+                        (warp - DRAIN_WARP0) * (32 * 33);
+        uint16_t* stB = reinterpret_cast<uint16_t*>(smem_raw + (base - smem_u32(smem_raw)) +
+                                                    DRAIN_WARPS * 32 * 33 * 4) +
+                        (warp - DRAIN_WARP0) * (32 * 34);
+        const int rb = row_a + quarter * 32;
+#pragma unroll
+        for (int ch = 0; ch < DCOLS / 32; ++ch) {
+          const int col = half * DCOLS + ch * 32;
+          const int c0 = row_b + col;
+          float trf = 0.0f, frf = 0.0f;
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int cs = c0 + hh * 16;
+            uint32_t m01[16], m2[16];
             if (bit) {
-              x = 2.0f * join_value<F>((uint16_t)(m01[j] & 0xffffu), (uint16_t)(m01[j] >> 16),
-                                       (uint16_t)m2[j]) -
-                  x;
-              if (SP && fabsf(x) < tau) x = 0.0f;  // prune the update
-            }
-            if (SP && x != 0.0f) nz = 1;
-            uint16_t a, b2, c2;
-            split_value_f<F>(x, a, b2, c2);
-            stA[lane * 33 + jj] = (uint32_t)a | ((uint32_t)b2 << 16);
-            if (fmt_bf16(F)) stB[lane * 34 + jj] = c2;
-            if (r <= c) {
-              if (r == c) {
-                trf += x;
-                frf += x * x;
-              } else {
-                frf += 2.0f * x * x;
-                // mirror (c, r): consecutive threads write consecutive r
-                const size_t m = (size_t)c * ld + r;
-                out0[m] = a;
-                out1[m] = b2;
-                if (fmt_bf16(F)) out2[m] = c2;
-                if (want_fp64) {
-                  if (df) {
-                    out_hi[m] = x;
-                    out_lo[m] = 0.0f;
-                  } else {
-                    out64[m] = (double)x;
-                  }
-                }
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const size_t m = (size_t)(cs + jj) * ld + r;
+                m01[jj] = (uint32_t)xs0[m] | ((uint32_t)xs1[m] << 16);
+                m2[jj] = fmt_bf16(F) ? (uint32_t)xs2[m] : 0u;
               }
-              if (want_fp64) {  // (r, c), a few products per solve: direct stores
-                const size_t d = (size_t)r * ld + c;
-                if (df) {
-                  out_hi[d] = x;
-                  out_lo[d] = 0.0f;
+            }
+            uint32_t u1[16], u2[16];
+            if (nkb > 0) {
+              tmem_ld16(lane_addr + 128u * C::NBUF + col + hh * 16, u1);
+              if (fmt_bf16(F)) tmem_ld16(lane_addr + 128u * (C::NBUF + 1) + col + hh * 16, u2);
+              tmem_ld_wait();
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) u1[jj] = u2[jj] = 0u;
+            }
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int jc = hh * 16 + jj;
+              const int c = cs + jj;
+              float x = sum0[ch * 32 + jc] * W::w0 + __uint_as_float(u1[jj]) * W::w1;
+              if (fmt_bf16(F)) x += __uint_as_float(u2[jj]) * W::w2;
+              if (fabsf(x) < tau) x = 0.0f;  // prune the product
+              if (bit) {
+                x = 2.0f * join_value<F>((uint16_t)(m01[jj] & 0xffffu),
+                                         (uint16_t)(m01[jj] >> 16), (uint16_t)m2[jj]) -
+                    x;
+                if (fabsf(x) < tau) x = 0.0f;  // prune the update
+              }
+              if (x != 0.0f) nz = 1;
+              uint16_t a, b2, c2;
+              split_value_f<F>(x, a, b2, c2);
+              stA[lane * 33 + jc] = (uint32_t)a | ((uint32_t)b2 << 16);
+              if (fmt_bf16(F)) stB[lane * 34 + jc] = c2;
+              if (r <= c) {
+                if (r == c) {
+                  trf += x;
+                  frf += x * x;
                 } else {
-                  out64[d] = (double)x;
+                  frf += 2.0f * x * x;
+                  const size_t m = (size_t)c * ld + r;
+                  out0[m] = a;
+                  out1[m] = b2;
+                  if (fmt_bf16(F)) out2[m] = c2;
                 }
               }
             }
           }
-        }
-        tr += (double)trf;
-        fr += (double)frf;
-        // (r, c) slices: 32 rows of 32 columns back out, one row per store
-        __syncwarp();
-        const int cc = c0 + lane;
+          tr += (double)trf;
+          fr += (double)frf;
+          __syncwarp();
+          const int cc = c0 + lane;
 #pragma unroll 4
-        for (int i = 0; i < 32; ++i) {
-          if (rb + i <= cc) {
-            const uint32_t v = stA[i * 33 + lane];
-            const size_t d = (size_t)(rb + i) * ld + cc;
-            out0[d] = (uint16_t)(v & 0xffffu);
-            out1[d] = (uint16_t)(v >> 16);
-            if (fmt_bf16(F)) out2[d] = stB[i * 34 + lane];
+          for (int i = 0; i < 32; ++i) {
+            if (rb + i <= cc) {
+              const uint32_t v = stA[i * 33 + lane];
+              const size_t d = (size_t)(rb + i) * ld + cc;
+              out0[d] = (uint16_t)(v & 0xffffu);
+              out1[d] = (uint16_t)(v >> 16);
+              if (fmt_bf16(F)) out2[d] = stB[i * 34 + lane];
+            }
           }
+          __syncwarp();
         }
-        __syncwarp();
+        // the staging area is the operand ring: order these generic-proxy
+        // writes before the next tile's TMA writes into it
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       }
-    }
-    tc_fence_before();
-    if (SP) {
+      tc_fence_before();
       const int any = __syncthreads_or(nz);
-      // (a skipped tile keeps its zeros: flag 0)
+      tc_fence_after();
       if (threadIdx.x == 0) {
-        buf.tflags[dst][(size_t)I * T + J] = (uint8_t)(any ? 1 : 0);
-        buf.tflags[dst][(size_t)J * T + I] = (uint8_t)(any ? 1 : 0);
+        fd[(size_t)I * T + J] = (uint8_t)(any ? 1 : 0);
+        fd[(size_t)J * T + I] = (uint8_t)(any ? 1 : 0);
       }
-    } else {
-      __syncthreads();
+      g += nkb;
+      gc += NC;
+      ++ntile;
+      if (*err) break;  // (uniform: read after the barrier above)
     }
+    __syncthreads();
     if (*err) {
       // failure path: let TMA copies still in flight land before the CTA exits
       if (threadIdx.x == 0) {
-        for (int kb = s_consumed; kb < issued; ++kb)
-          mbar_wait(full_bar(kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, err, false,
+        for (int gq = s_consumed; gq < issued; ++gq)
+          mbar_wait(full_bar(gq % C::STAGES), (uint32_t)(gq / C::STAGES) & 1u, err, false,
                     kWaitLimitNs / 10);
       }
       __syncthreads();
@@ -462,7 +783,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       st->status = PROGRESS_ETIMEOUT;
       st->done = 1;
     }
-  }  // !skip_cta
+  }
 
   block_sum2(tr, fr, s_scratch);
   if (threadIdx.x == 0) {
@@ -481,7 +802,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       st->t2 = b;
       st->iter = k_iter + 1;
       st->phase_iters[kPhaseSplit] += 1;
-      st->x_fp64_valid = want_fp64 ? 1 : 0;
+      st->x_fp64_valid = 0;
       st->x_slices_valid = 1;
       decide(st);
     }
@@ -546,23 +867,45 @@ cudaError_t launch_square_split(const DevBuffers& b, const SolveParams& p,
   if (tiles > b.max_partials) return cudaErrorInvalidValue;
   TensorMaps maps;
   if (!encode_maps(b, ld, p.slice_fmt, &maps)) return cudaErrorInvalidValue;
-  const bool sparse = p.tau > 0.0f;
-  if (sparse && p.slice_fmt != kFP16x2 && p.slice_fmt != kBF16x3) return cudaErrorInvalidValue;
-  switch (p.slice_fmt * 2 + (sparse ? 1 : 0)) {
-#define SP2_SQS(F, SPARSE)                                                                \
-  case F * 2 + (SPARSE ? 1 : 0): {                                                       \
-    const int smem = Cfg<F>::SMEM;                                                        \
-    cudaFuncSetAttribute(square_split_kernel<F, SPARSE>,                                  \
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);              \
-    square_split_kernel<F, SPARSE><<<tiles, THREADS, smem, s>>>(maps, b, cond_handle, p.tau); \
-    break;                                                                                \
+  if (p.tau > 0.0f) {
+    if (p.slice_fmt != kFP16x2 && p.slice_fmt != kBF16x3) return cudaErrorInvalidValue;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // one CTA per SM, at most SP_MAX_TILES tiles each, never more CTAs than tiles
+    int grid = nsm < tiles ? nsm : tiles;
+    if ((tiles + grid - 1) / grid > SP_MAX_TILES) grid = (tiles + SP_MAX_TILES - 1) / SP_MAX_TILES;
+    switch (p.slice_fmt) {
+#define SP2_SQP(F)                                                                          \
+  case F: {                                                                                 \
+    const int smem = Cfg<F>::SMEM;                                                          \
+    cudaFuncSetAttribute(square_split_sparse_kernel<F>,                                     \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);                \
+    square_split_sparse_kernel<F><<<grid, THREADS, smem, s>>>(maps, b, cond_handle, p.tau); \
+    break;                                                                                  \
   }
-    SP2_SQS(kFP16x2, false)
-    SP2_SQS(kBF16x3, false)
-    SP2_SQS(kFP16x2F, false)
-    SP2_SQS(kBF16x3F, false)
-    SP2_SQS(kFP16x2, true)
-    SP2_SQS(kBF16x3, true)
+      SP2_SQP(kFP16x2)
+      SP2_SQP(kBF16x3)
+#undef SP2_SQP
+      default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  switch (p.slice_fmt) {
+#define SP2_SQS(F)                                                                     \
+  case F: {                                                                            \
+    const int smem = Cfg<F>::SMEM;                                                     \
+    cudaFuncSetAttribute(square_split_kernel<F>,                                       \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);           \
+    square_split_kernel<F><<<tiles, THREADS, smem, s>>>(maps, b, cond_handle);         \
+    break;                                                                             \
+  }
+    SP2_SQS(kFP16x2)
+    SP2_SQS(kBF16x3)
+    SP2_SQS(kFP16x2F)
+    SP2_SQS(kBF16x3F)
 #undef SP2_SQS
     default:
       return cudaErrorInvalidValue;
