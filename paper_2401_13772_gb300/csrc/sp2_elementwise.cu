@@ -118,17 +118,17 @@ __global__ void __launch_bounds__(kEwThreads) x0_kernel(const double* __restrict
   float* Xf = reinterpret_cast<float*>(X);
   const size_t plane = (size_t)ld * ld;
   double tr = 0.0, fr = 0.0;
-  for (int64_t r = blockIdx.x; r < ld; r += gridDim.x) {
-    for (int64_t c = threadIdx.x; c < ld; c += kEwThreads) {
-      const size_t idx = (size_t)r * ld + c;
-      double x = 0.0;
-      if (r < n && c < n) {
-        const double h = H[r * n + c];
-        x = ((r == c) ? (emax - h) : -h) * inv_w;
-        if (r == c) tr += x;
-        fr += x * x;
-      }
-      if (write_fp64) {
+  if (write_fp64) {
+    for (int64_t r = blockIdx.x; r < ld; r += gridDim.x) {
+      for (int64_t c = threadIdx.x; c < ld; c += kEwThreads) {
+        const size_t idx = (size_t)r * ld + c;
+        double x = 0.0;
+        if (r < n && c < n) {
+          const double h = H[r * n + c];
+          x = ((r == c) ? (emax - h) : -h) * inv_w;
+          if (r == c) tr += x;
+          fr += x * x;
+        }
         if (df64) {
           const float h = (float)x;
           Xf[idx] = h;
@@ -136,8 +136,33 @@ __global__ void __launch_bounds__(kEwThreads) x0_kernel(const double* __restrict
         } else {
           X[idx] = x;
         }
+        if (write_slices) store_slices<F>(S, idx, x);
       }
-      if (write_slices) store_slices<F>(S, idx, x);
+    }
+  } else {
+    // split products from the start: X0 is only needed as slices (22 / 24
+    // significant bits), so it is formed in FP32 (one FP64-to-FP32 conversion
+    // per element) and the traces are summed in FP32 along each row segment,
+    // then folded into FP64
+    const float emax_f = (float)emax, inv_w_f = (float)inv_w;
+    for (int64_t r = blockIdx.x; r < ld; r += gridDim.x) {
+      float frf = 0.0f;
+      for (int64_t c = threadIdx.x; c < ld; c += kEwThreads) {
+        const size_t idx = (size_t)r * ld + c;
+        float x = 0.0f;
+        if (r < n && c < n) {
+          const float h = (float)H[r * n + c];
+          x = ((r == c) ? (emax_f - h) : -h) * inv_w_f;
+          if (r == c) tr += (double)x;
+          frf += x * x;
+        }
+        uint16_t a, b, cc;
+        split_value_f<F>(x, a, b, cc);
+        S.s[0][idx] = a;
+        S.s[1][idx] = b;
+        if (fmt_bf16(F)) S.s[2][idx] = cc;
+      }
+      fr += (double)frf;
     }
   }
   block_sum2(tr, fr, scratch);
@@ -181,8 +206,12 @@ __global__ void __launch_bounds__(kEwThreads) finalize_kernel(const State* __res
       double v;
       if (from64) {
         v = df64 ? (double)Xf[src] + (double)Xf[plane + src] : X[src];
+      } else if (!fmt_bf16(F)) {
+        // joined in FP32 (FP64 arithmetic is scarce here): within 2^-24 of the
+        // value, below the 2^-22 resolution of the two FP16 slices themselves
+        v = (double)join_value<F>(s0[src], s1[src], (uint16_t)0);
       } else {
-        v = join_value_d<F>(s0[src], s1[src], fmt_bf16(F) ? s2[src] : (uint16_t)0);
+        v = join_value_d<F>(s0[src], s1[src], s2[src]);
       }
       D[r * n + c] = v;
     }
