@@ -43,8 +43,8 @@ OZ_KERNEL = ("square_oz_kernel (BF16 digit products, tcgen05; time includes digi
 # stands, keyed by (kernel, n); see profiles/.
 NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200,
                ("square_df64_kernel (double-float, FP32 pipe)", 4096): 521512448,
-               ("square_split_kernel (tcgen05)", 4096): 161894656,
-               (OZ_KERNEL, 4096): 658666752}
+               ("square_split_kernel (tcgen05)", 4096): 155314688,
+               (OZ_KERNEL, 4096): 658146304}
 NOMINAL_FP64_TFLOPS = 1.25
 DF_OPS = 12  # FP32 instructions per double-float multiply-add in square_df64_kernel
 OZ_PRODUCTS = 15  # BF16 digit products per FP64-accurate product in square_oz_kernel
