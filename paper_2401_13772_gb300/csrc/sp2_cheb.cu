@@ -21,8 +21,8 @@
 //                        runs them on concurrent streams; here they share one
 //                        launch). Then the m - 1 nested products
 //                        P_j = S_j + T_k P_{j+1}; the last writes D in FP64.
-//   cheb_sum16_kernel /  every S_j in one pass over T_1..T_{k-1} (the sums
-//   cheb_sum_kernel      are independent, Eq. 9); the first for k, m <= 16
+//   cheb_sum_fast_kernel every S_j in one pass over T_1..T_{k-1} (the sums
+//                        are independent, Eq. 9), coefficients in the constant bank
 //
 // Every matrix is a polynomial in Ht, so all of them are symmetric and
 // commute: a product tile (I, J), I <= J, reads the row panels I of A and J
@@ -403,116 +403,105 @@ __global__ void __launch_bounds__(EW_THREADS)
 
 // S_j = sum_{i<k} d_ij T_i for every j (T_0 = I, T_i in slot i - 1), stored as
 // slices of S_j / s_j in slot k + j; with m == 1, S_0 goes to D in FP64.
-template <int F>
+// The same pass with the coefficients as kernel parameters: a zero-padded
+// KB x MB table in the constant bank, so every multiply-add of the fully
+// unrolled loops takes its coefficient as an immediate constant operand. Table
+// sizes 16 x 16 (two neighbouring elements per thread, 32-bit slice loads and
+// stores), 32 x 32 and 64 x 64 (one element per thread; up to 16.6 KB of
+// kernel parameters).
+template <int KB, int MB>
+struct SumTable {
+  float d[KB * MB];  // d_ij at i MB + j, zero outside i < k, j < m
+  float inv_s[MB];
+};
+
+template <int F, int KB, int MB, int EPT>
 __global__ void __launch_bounds__(EW_THREADS)
-    cheb_sum_kernel(Pool pool, int ld, int k, int m, const float* __restrict__ dcoef,
-                    const float* __restrict__ inv_s, double* __restrict__ D, int64_t n,
-                    const int* __restrict__ gerr) {
-  __shared__ float s_d[MAX_K * MAX_M];
-  __shared__ float s_inv[MAX_M];
-  __shared__ int s_skip;
-  if (threadIdx.x == 0) s_skip = *(volatile const int*)gerr;
-  __syncthreads();
-  if (s_skip) return;
-  for (int i = threadIdx.x; i < k * m; i += EW_THREADS) s_d[i] = dcoef[i];  // d[i][j] at i m + j
-  for (int j = threadIdx.x; j < m; j += EW_THREADS) s_inv[j] = inv_s[j];
-  __syncthreads();
+    cheb_sum_fast_kernel(Pool pool, int ld, int k, int m,
+                         const __grid_constant__ SumTable<KB, MB> tab, double* __restrict__ D,
+                         int64_t n, const int* __restrict__ gerr) {
+  static_assert(EPT == 1 || EPT == 2, "one or two elements per thread");
+  if (*(volatile const int*)gerr) return;  // no barrier below: a per-thread exit is safe
   const size_t area = (size_t)ld * ld;
-  for (size_t e = (size_t)blockIdx.x * EW_THREADS + threadIdx.x; e < area;
-       e += (size_t)gridDim.x * EW_THREADS) {
+  const size_t groups = area / EPT;  // ld is even: a pair shares a row
+  for (size_t q = (size_t)blockIdx.x * EW_THREADS + threadIdx.x; q < groups;
+       q += (size_t)gridDim.x * EW_THREADS) {
+    const size_t e = EPT * q;
     const int64_t r = (int64_t)(e / ld), c = (int64_t)(e - (size_t)r * ld);
-    float t[MAX_K];
-    t[0] = (r == c) ? 1.0f : 0.0f;
+    float t[EPT][KB];
 #pragma unroll
-    for (int i = 1; i < MAX_K; ++i) {
-      t[i] = 0.0f;
+    for (int u = 0; u < EPT; ++u) t[u][0] = (r == c + u) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int i = 1; i < KB; ++i) {
+#pragma unroll
+      for (int u = 0; u < EPT; ++u) t[u][i] = 0.0f;
       if (i < k) {
         const size_t o = (size_t)(i - 1) * area + e;
-        t[i] = join_value<F>(pool.s[0][o], pool.s[1][o], fmt_bf16(F) ? pool.s[2][o] : (uint16_t)0);
+        if (EPT == 2) {
+          const uint32_t h = *reinterpret_cast<const uint32_t*>(pool.s[0] + o);
+          const uint32_t l = *reinterpret_cast<const uint32_t*>(pool.s[1] + o);
+          const uint32_t w =
+              fmt_bf16(F) ? *reinterpret_cast<const uint32_t*>(pool.s[2] + o) : 0u;
+          t[0][i] = join_value<F>((uint16_t)(h & 0xffffu), (uint16_t)(l & 0xffffu),
+                                  (uint16_t)(w & 0xffffu));
+          t[EPT - 1][i] = join_value<F>((uint16_t)(h >> 16), (uint16_t)(l >> 16),
+                                        (uint16_t)(w >> 16));
+        } else {
+          t[0][i] = join_value<F>(pool.s[0][o], pool.s[1][o],
+                                  fmt_bf16(F) ? pool.s[2][o] : (uint16_t)0);
+        }
       }
     }
-    for (int j = 0; j < m; ++j) {
-      float acc = 0.0f;
 #pragma unroll
-      for (int i = 0; i < MAX_K; ++i)
-        if (i < k) acc += s_d[i * m + j] * t[i];
-      if (m == 1) {
-        if (r < n && c < n) D[r * n + c] = (double)acc;
-      } else {
-        uint16_t s0, s1, s2;
-        split_value_f<F>(acc * s_inv[j], s0, s1, s2);
-        const size_t o = (size_t)(k + j) * area + e;
-        pool.s[0][o] = s0;
-        pool.s[1][o] = s1;
-        if (fmt_bf16(F)) pool.s[2][o] = s2;
+    for (int j = 0; j < MB; ++j) {
+      if (j < m) {
+        float acc[EPT];
+#pragma unroll
+        for (int u = 0; u < EPT; ++u) acc[u] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < KB; ++i) {
+#pragma unroll
+          for (int u = 0; u < EPT; ++u) acc[u] += tab.d[i * MB + j] * t[u][i];
+        }
+        if (m == 1) {
+#pragma unroll
+          for (int u = 0; u < EPT; ++u)
+            if (r < n && c + u < n) D[r * n + c + u] = (double)acc[u];
+        } else {
+          uint16_t x[EPT][3];
+#pragma unroll
+          for (int u = 0; u < EPT; ++u)
+            split_value_f<F>(acc[u] * tab.inv_s[j], x[u][0], x[u][1], x[u][2]);
+          const size_t o = (size_t)(k + j) * area + e;
+          if (EPT == 2) {
+#pragma unroll
+            for (int sl = 0; sl < fmt_slices(F); ++sl)
+              *reinterpret_cast<uint32_t*>(pool.s[sl] + o) =
+                  (uint32_t)x[0][sl] | ((uint32_t)x[EPT - 1][sl] << 16);
+          } else {
+#pragma unroll
+            for (int sl = 0; sl < fmt_slices(F); ++sl) pool.s[sl][o] = x[0][sl];
+          }
+        }
       }
     }
   }
 }
 
-// The same pass for k, m <= 16 with the coefficients as kernel parameters (a
-// zero-padded 16 x 16 table in the constant bank: every multiply-add of the
-// fully unrolled loops takes its coefficient as an immediate constant operand)
-// and two neighbouring elements per thread (32-bit slice loads and stores).
-constexpr int SUM_K = 16;
-struct SumTable {
-  float d[SUM_K * SUM_K];  // d_ij at i SUM_K + j, zero outside i < k, j < m
-  float inv_s[SUM_K];
-};
-
-template <int F>
-__global__ void __launch_bounds__(EW_THREADS)
-    cheb_sum16_kernel(Pool pool, int ld, int k, int m, const __grid_constant__ SumTable tab,
-                      double* __restrict__ D, int64_t n, const int* __restrict__ gerr) {
-  if (*(volatile const int*)gerr) return;  // no barrier below: a per-thread exit is safe
-  const size_t area = (size_t)ld * ld;
-  const size_t pairs = area / 2;
-  for (size_t q = (size_t)blockIdx.x * EW_THREADS + threadIdx.x; q < pairs;
-       q += (size_t)gridDim.x * EW_THREADS) {
-    const size_t e = 2 * q;  // ld is even: e and e + 1 share a row
-    const int64_t r = (int64_t)(e / ld), c = (int64_t)(e - (size_t)r * ld);
-    float t0[SUM_K], t1[SUM_K];
-    t0[0] = (r == c) ? 1.0f : 0.0f;
-    t1[0] = (r == c + 1) ? 1.0f : 0.0f;
-#pragma unroll
-    for (int i = 1; i < SUM_K; ++i) {
-      t0[i] = 0.0f;
-      t1[i] = 0.0f;
-      if (i < k) {
-        const size_t o = (size_t)(i - 1) * area + e;
-        const uint32_t h = *reinterpret_cast<const uint32_t*>(pool.s[0] + o);
-        const uint32_t l = *reinterpret_cast<const uint32_t*>(pool.s[1] + o);
-        const uint32_t w = fmt_bf16(F) ? *reinterpret_cast<const uint32_t*>(pool.s[2] + o) : 0u;
-        t0[i] = join_value<F>((uint16_t)(h & 0xffffu), (uint16_t)(l & 0xffffu),
-                              (uint16_t)(w & 0xffffu));
-        t1[i] = join_value<F>((uint16_t)(h >> 16), (uint16_t)(l >> 16), (uint16_t)(w >> 16));
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < SUM_K; ++j) {
-      if (j < m) {
-        float a0 = 0.0f, a1 = 0.0f;
-#pragma unroll
-        for (int i = 0; i < SUM_K; ++i) {
-          a0 += tab.d[i * SUM_K + j] * t0[i];
-          a1 += tab.d[i * SUM_K + j] * t1[i];
-        }
-        if (m == 1) {
-          if (r < n && c < n) D[r * n + c] = (double)a0;
-          if (r < n && c + 1 < n) D[r * n + c + 1] = (double)a1;
-        } else {
-          uint16_t x0, x1, x2, y0, y1, y2;
-          split_value_f<F>(a0 * tab.inv_s[j], x0, x1, x2);
-          split_value_f<F>(a1 * tab.inv_s[j], y0, y1, y2);
-          const size_t o = (size_t)(k + j) * area + e;
-          *reinterpret_cast<uint32_t*>(pool.s[0] + o) = (uint32_t)x0 | ((uint32_t)y0 << 16);
-          *reinterpret_cast<uint32_t*>(pool.s[1] + o) = (uint32_t)x1 | ((uint32_t)y1 << 16);
-          if (fmt_bf16(F))
-            *reinterpret_cast<uint32_t*>(pool.s[2] + o) = (uint32_t)x2 | ((uint32_t)y2 << 16);
-        }
-      }
-    }
-  }
+template <int F, int KB, int MB, int EPT>
+cudaError_t launch_sum_fast(const Pool& pool, int ld, int k, int m, const std::vector<float>& d,
+                            const std::vector<float>& inv_s, double* D, int64_t n,
+                            const int* err, cudaStream_t s) {
+  SumTable<KB, MB> tab;
+  memset(&tab, 0, sizeof tab);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < m; ++j) tab.d[i * MB + j] = d[(size_t)i * m + j];
+  for (int j = 0; j < m; ++j) tab.inv_s[j] = inv_s[j];
+  const unsigned blocks = (unsigned)std::min<size_t>(
+      EW_BLOCKS, ((size_t)ld * ld / EPT + EW_THREADS - 1) / EW_THREADS);
+  cheb_sum_fast_kernel<F, KB, MB, EPT><<<blocks, EW_THREADS, 0, s>>>(pool, ld, k, m, tab, D, n,
+                                                                     err);
+  return cudaGetLastError();
 }
 
 __global__ void cheb_trace_kernel(const double* __restrict__ D, int64_t n, double* out) {
@@ -598,8 +587,6 @@ struct ChebWs {
   size_t pool_cap = 0;       // elements
   Prod* prods = nullptr;
   size_t prods_cap = 0;
-  float* dcoef = nullptr;
-  float* inv_s = nullptr;
   int* err = nullptr;
   double* scal = nullptr;    // [0..1] bounds, [2] trace
   int last_ld = 0, last_slots = 0, last_ns = 0;  // layout of the last solve's stack
@@ -777,10 +764,6 @@ progress_status_t run(const double* dH, int64_t n, double mu, double beta, int k
   if (!w->err) {
     if ((e = cudaMalloc(&w->err, sizeof(int))) != cudaSuccess) return ccuda(e, "cheb alloc");
     if ((e = cudaMalloc(&w->scal, 4 * sizeof(double))) != cudaSuccess) return ccuda(e, "cheb alloc");
-    if ((e = cudaMalloc(&w->dcoef, MAX_K * MAX_M * sizeof(float))) != cudaSuccess)
-      return ccuda(e, "cheb alloc");
-    if ((e = cudaMalloc(&w->inv_s, MAX_M * sizeof(float))) != cudaSuccess)
-      return ccuda(e, "cheb alloc");
   }
   const size_t need = (size_t)NS * nslots * (size_t)ld * ld;
   if (need > w->pool_cap) {
@@ -836,12 +819,6 @@ progress_status_t run(const double* dH, int64_t n, double mu, double beta, int k
   if (e == cudaSuccess && nprod > 0)
     e = cudaMemcpyAsync(w->prods, prods.data(), prods.size() * sizeof(Prod),
                         cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(w->dcoef, dcoef.data(), dcoef.size() * sizeof(float),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(w->inv_s, inv_s.data(), inv_s.size() * sizeof(float),
-                        cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return ccuda(e, "cheb set-up upload");
   int launches = h_bounds ? 0 : 2;  // state init + Gershgorin
   const unsigned ew_blocks =
@@ -856,20 +833,13 @@ progress_status_t run(const double* dH, int64_t n, double mu, double beta, int k
     ++launches;
     first = end;
   }
-  if (k <= SUM_K && m <= SUM_K) {
-    SumTable tab;
-    memset(&tab, 0, sizeof tab);
-    for (int i = 0; i < k; ++i)
-      for (int j = 0; j < m; ++j) tab.d[i * SUM_K + j] = dcoef[(size_t)i * m + j];
-    for (int j = 0; j < m; ++j) tab.inv_s[j] = inv_s[j];
-    const unsigned pair_blocks = (unsigned)std::min<size_t>(
-        EW_BLOCKS, ((size_t)ld * ld / 2 + EW_THREADS - 1) / EW_THREADS);
-    cheb_sum16_kernel<F><<<pair_blocks, EW_THREADS, 0, s>>>(pool, ld, k, m, tab, dD, n, w->err);
-  } else {
-    cheb_sum_kernel<F><<<ew_blocks, EW_THREADS, 0, s>>>(pool, ld, k, m, w->dcoef, w->inv_s, dD,
-                                                        n, w->err);
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) return ccuda(e, "cheb_sum launch");
+  if (k <= 16 && m <= 16)
+    e = launch_sum_fast<F, 16, 16, 2>(pool, ld, k, m, dcoef, inv_s, dD, n, w->err, s);
+  else if (k <= 32 && m <= 32)
+    e = launch_sum_fast<F, 32, 32, 1>(pool, ld, k, m, dcoef, inv_s, dD, n, w->err, s);
+  else
+    e = launch_sum_fast<F, 64, 64, 1>(pool, ld, k, m, dcoef, inv_s, dD, n, w->err, s);
+  if (e != cudaSuccess) return ccuda(e, "cheb_sum launch");
   ++launches;
   for (int q = t_products; q < nprod; ++q) {
     e = launch_products<F>(maps, pool, w->prods + q, 1, ld, dD, n, w->err, s);
@@ -907,7 +877,7 @@ void cheb_release(int dev, cudaStream_t s, bool all_streams) {
   for (auto it = g_cws.begin(); it != g_cws.end();) {
     if (it->first.first == dev && (all_streams || it->first.second == s)) {
       ChebWs* w = it->second;
-      void* ptrs[] = {w->pool, w->prods, w->dcoef, w->inv_s, w->err, w->scal};
+      void* ptrs[] = {w->pool, w->prods, w->err, w->scal};
       for (void* p : ptrs)
         if (p) cudaFree(p);
       delete w;

@@ -42,8 +42,9 @@ def gate(ref, beta, prec):
     return 8.0 * 2.0 ** -23 * g * slope
 
 
+# (the S_j pass takes its coefficient table in 16 x 16, 32 x 32 or 64 x 64 form)
 CASES = [(75, 16, 16), (75, 8, 4), (75, 5, 3), (75, 1, 6), (75, 7, 1), (75, 1, 1), (32, 16, 16),
-         (33, 4, 8)]
+         (33, 4, 8), (33, 20, 20), (33, 40, 3), (33, 64, 2)]
 
 
 @pytest.mark.parametrize("prec", ["fp32_split", "fp32_split_bf16"])
