@@ -52,8 +52,17 @@ __global__ void __launch_bounds__(kEwThreads) gershgorin_kernel(const double* __
   double lo = INFINITY, hi = -INFINITY;
   for (int64_t i = (int64_t)blockIdx.x * (kEwThreads / 32) + wid; i < n; i += warps) {
     const double* row = H + i * n;
-    double r = 0.0;
-    for (int64_t j = lane; j < n; j += 32) r += (j == i) ? 0.0 : fabs(row[j]);
+    // four independent partial sums per lane keep four loads in flight
+    double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+    int64_t j = lane;
+    for (; j + 96 < n; j += 128) {
+      r0 += (j == i) ? 0.0 : fabs(row[j]);
+      r1 += (j + 32 == i) ? 0.0 : fabs(row[j + 32]);
+      r2 += (j + 64 == i) ? 0.0 : fabs(row[j + 64]);
+      r3 += (j + 96 == i) ? 0.0 : fabs(row[j + 96]);
+    }
+    for (; j < n; j += 32) r0 += (j == i) ? 0.0 : fabs(row[j]);
+    double r = (r0 + r1) + (r2 + r3);
     r = warp_sum(r);
     const double d = row[i];
     lo = fmin(lo, d - r);
