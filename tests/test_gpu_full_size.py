@@ -7,7 +7,10 @@ element by element (about 20 s of numpy on the host). N = 8192 (2048 sites):
 properties that hold at any size, on sampled rows -- symmetry, Tr D = Nocc,
 D^2 = D and [H, D] = 0 -- with the exact gate on Tr D. 4000 batched parts:
 the autotuned launch, then 40 parts sampled across the size range, each
-against the oracle's plain FP64 SP2.
+against the oracle's plain FP64 SP2. The Chebyshev workload (N = 4096, L + 1 =
+256): the whole D against the oracle's evaluation of the same expansion. The
+thresholded workload (N = 16384 chain, tau = 1e-6): sampled rows against the
+exact projector's band.
 """
 
 import numpy as np
@@ -92,3 +95,43 @@ def test_4000_part_batch_sampled_parts_match_oracle(pkg):
         gate = 0.2 * 2.0 ** -22 / relgap + 1e-6   # as in test_gpu_batched.py
         assert float(np.abs(Di - ref).max()) <= gate, (i, k)
         assert abs(np.trace(Di) - nocc[i]) <= 4e-6 * k
+
+
+def test_cheb_n4096_matches_oracle_elementwise(pkg):
+    # the Chebyshev workload of the benchmark: C1's H, mu = 0.5 eV, beta = 1 / eV,
+    # L + 1 = 256 (k = m = 16); the whole D against the oracle's FP64 evaluation of
+    # the same expansion (gate as in test_gpu_cheb: 8 g max(1, beta b / 4) 2^-23)
+    import torch
+    from oracle import cheb as C
+    H, _ = cube_hamiltonian(1024, 0)
+    D, info = pkg.cheb_fermi(torch.from_numpy(H).to("cuda:0"), 0.5, 1.0, 16, 16)
+    ref = C.fermi_operator(H, 0.5, 1.0, 16, 16)
+    gate = 8.0 * 2.0 ** -23 * max(1.0, float(np.abs(ref["d"]).sum())) * max(1.0, ref["b"] / 4.0)
+    err = float(np.abs(D.cpu().numpy() - ref["D"]).max())
+    assert info["products"] == 30 and err <= gate, (err, gate)
+
+
+def test_thresholded_n16384_chain_against_exact_band(pkg):
+    # the thresholded workload of the benchmark: the N = 16384 dimerized chain,
+    # tau = 1e-6; 64 sampled rows against the exact projector of a 512-site chain
+    # (the same entries within 256 sites of the diagonal), zero beyond the band
+    import torch
+    from workloads import chain_hamiltonian
+    n = 16384
+    H, nocc = chain_hamiltonian(n, -1.0, -0.6)
+    D, info = pkg.sp2_dense_ex(torch.from_numpy(H).to("cuda:0"), nocc, 1e-9,
+                               prec="fp32_split", tau=1e-6)
+    assert info["status"] == "OK" and info["converged"]
+    Hs, ns = chain_hamiltonian(512, -1.0, -0.6)
+    w, V = oracle.jacobi_eigh(Hs)
+    P, _ = oracle.density_projector(w, V, ns)
+    rows = np.linspace(0, n - 1, 64).astype(np.int64)
+    Dn = D[torch.from_numpy(rows).to("cuda:0")].cpu().numpy()
+    for k, r in enumerate(rows):
+        off = (np.arange(n) - r + n // 2) % n - n // 2
+        band = np.abs(off) < 256
+        ref = P[r % 2, (r % 2 + off[band]) % 512]
+        assert float(np.abs(Dn[k, band] - ref).max()) <= 4e-6 + 2e-5
+        assert not Dn[k, ~band].any()
+    T = n // 128
+    assert info["kblocks"] < 1e-3 * info["iters"] * T * (T + 1) // 2 * (n // 64)
