@@ -319,6 +319,31 @@ def cheb_plan(k, m, mu, beta, emin, emax):
             "slots": int(counts[2]), "t_products": int(counts[3])}
 
 
+def cheb_choose_km(terms, mu, beta, emin, emax, max_growth=8.0):
+    """Pick (k, m) for cheb_fermi with k m >= terms: the fewest matrix products
+    ((k - 1) + (m - 1)) among the splits whose nested sums stay within max_growth
+    (the plan's growth = sum |d_ij|; a large growth amplifies the products'
+    rounding, e.g. k = m = 32 at beta b = 236 gives 3e5). Ties go to fewer terms.
+    Host only (uses cheb_plan). Raises ValueError if no split qualifies."""
+    import math
+    best = None
+    for k in range(1, 65):
+        m = max(1, math.ceil(terms / k))
+        if m > 64:
+            continue
+        plan = cheb_plan(k, m, mu, beta, emin, emax)
+        growth = float(abs(plan["d"]).sum())
+        if growth > max_growth:
+            continue
+        key = ((k - 1) + (m - 1), k * m)
+        if best is None or key < best[0]:
+            best = (key, k, m, growth)
+    if best is None:
+        raise ValueError("no (k, m) with k m >= terms keeps the growth within max_growth")
+    return {"k": best[1], "m": best[2], "products": best[0][0], "terms": best[0][1],
+            "growth": best[3]}
+
+
 def history(stream=None, cap=256):
     """(idem, margin) numpy arrays of the last solve on the stream: idem[k] =
     |Tr X_k^2 - Tr X_k|, margin[k] = signed branch-rule margin of product k."""

@@ -118,3 +118,32 @@ def test_chain_low_temperature_schedule(pkg):
     w, V = np.linalg.eigh(H)
     P = V[:, :nocc] @ V[:, :nocc].T
     assert np.abs(D - P).max() <= 1e-6 and peak <= 1.0 + 1e-9
+
+
+def test_chooser_prefers_stable_splits(pkg):
+    emin, emax = -58.86, 59.68  # the 4096-orbital cube's Gershgorin interval
+    r = pkg.cheb_choose_km(256, 0.5, 1.0, emin, emax)
+    assert (r["k"], r["m"], r["products"]) == (16, 16, 30) and r["growth"] <= 8.0
+    # a sharp Fermi function: the square split k = m = 32 grows to ~1e5; the
+    # chooser keeps the growth bounded with a few more products
+    sharp = pkg.cheb_plan(32, 32, 0.5, 4.0, emin, emax)
+    assert float(np.abs(sharp["d"]).sum()) > 1e4
+    r = pkg.cheb_choose_km(1024, 0.5, 4.0, emin, emax)
+    assert r["k"] * r["m"] >= 1024 and r["growth"] <= 8.0 and r["k"] > r["m"]
+    # every split with fewer products exceeds the growth bound
+    for k in range(1, 65):
+        m = -(-1024 // k)
+        if m <= 64 and (k - 1) + (m - 1) < r["products"]:
+            assert float(np.abs(pkg.cheb_plan(k, m, 0.5, 4.0, emin, emax)["d"]).sum()) > 8.0
+    with pytest.raises(ValueError):
+        pkg.cheb_choose_km(1024, 0.5, 4.0, emin, emax, max_growth=1e-3)
+
+
+def test_chosen_split_reproduces_the_oracle(pkg):
+    H, _ = cube_hamiltonian(24, 3)
+    ref0 = C.fermi_operator(H, 0.3, 2.0, 4, 4)  # only for the bounds
+    r = pkg.cheb_choose_km(200, 0.3, 2.0, ref0["emin"], ref0["emax"])
+    ref = C.fermi_operator(H, 0.3, 2.0, r["k"], r["m"])
+    plan = pkg.cheb_plan(r["k"], r["m"], 0.3, 2.0, ref["emin"], ref["emax"])
+    D, peak = execute(plan, H, r["k"], r["m"])
+    assert np.abs(D - ref["D"]).max() <= 1e-11 * max(1.0, r["growth"]) and peak <= 1.0 + 1e-9
