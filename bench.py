@@ -1,18 +1,23 @@
 #!/usr/bin/env python
 """SP2 density-matrix solves per second on one GB300, through the C ABI.
 
-Workload: the random-cube tight-binding Hamiltonian with 1024 sites x 4
-orbitals (N = 4096, Nocc = 2048, seed 0), the paper-shaped stand-in for the
-dense SP2 benchmarks of arXiv 2401.13772 (§VI). One step = one whole solve:
+Workload (default): the random-cube tight-binding Hamiltonian with 2048 sites x
+4 orbitals (N = 8192, Nocc = 4096, seed 0), the paper-shaped stand-in for the
+dense SP2 benchmarks of arXiv 2401.13772 (§VI), solved in mixed precision: FP16
+hi+lo split squarings on the tensor cores between an FP64-accurate prefix and an
+FP64-accurate refinement, FP64 traces and decisions. One step = one whole solve:
 Gershgorin bounds, X0 map, the SP2 product loop (decided on the device), and
-the copy of D. Inputs are resident in HBM; L2 is flushed (256 MiB write)
-before every timed step, outside its events.
+the copy of D. Inputs are resident in HBM; L2 is flushed (256 MiB write) before
+every timed step, outside its events.
 
-The JSON line also carries: the end-to-end rate through the same C ABI with
+The JSON line also carries: the same solve with BF16 hi+mid+lo split squarings
+(its own rate and D check), the end-to-end rate through the same C ABI with
 host buffers (H host->device and D device->host inside the timed region), the
-roofline of the product kernel, the plain FP64 SP2 rate on the same GPU when
-the headline mode is split precision, accuracy invariants of D, clocks
-sampled during the timed region, and the CPU oracle timed on a bounded sample.
+roofline of the product kernels, the plain FP64 SP2 rate on the same GPU, the
+element-wise error of every D against one whole solve of the CPU oracle (plain
+FP64 SP2), clocks sampled during the timed region, and that oracle solve's time
+on the host cores. `--sites 1024 --prec fp64` (or fp32_split) measures the
+N = 4096 plain FP64 (or FP32-split) solve with the same checks.
 
 --impl reference times the CPU oracle (plain FP64 SP2, numpy) on the host
 cores instead, on a bounded sample of the same workload.
@@ -46,6 +51,10 @@ NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200,
                ("square_split_kernel (tcgen05)", 4096): 155314688,
                (OZ_KERNEL, 4096): 658146304}
 NOMINAL_FP64_TFLOPS = 1.25
+# FP32-class (all split) solves: no tolerance is stated for them. Gate used:
+# max |D - D_ref| <= 1e-4 and |Tr D - Nocc| <= 4 n 2^-22 (the split phase stops
+# on its round-off floor, about n times the slices' 2^-22 resolution)
+FP32_GATE = {"max_abs_err": 1e-4, "trace_err_per_n": 4.0 * 2.0 ** -22}
 DF_OPS = 12  # FP32 instructions per double-float multiply-add in square_df64_kernel
 OZ_PRODUCTS = 15  # BF16 digit products per FP64-accurate product in square_oz_kernel
 IMPL_DTYPE = {"double-float": "double-float", "native fp64": "f64",
@@ -75,11 +84,13 @@ def parse_args():
     ap.add_argument("--fp64-impl", type=int, default=0, choices=[0, 1, 2, 3],
                     help="mixed modes, FP64-accurate products: 0 = library default, 1 = native "
                          "FP64, 2 = double-float, 3 = tensor-core digit products")
-    ap.add_argument("--sites", type=int, default=1024)
+    ap.add_argument("--sites", type=int, default=2048)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--fp64-prefix", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bf16-leg", dest="bf16_leg", action="store_false",
+                    help="mixed_fp16 runs: skip the same solve with bf16 hi+mid+lo splits")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true",
@@ -88,7 +99,7 @@ def parse_args():
                     help="0: device-driven WHILE graph; 1: plain launches (profilers)")
     ap.add_argument("--workload", default="dense",
                     choices=["dense", "batched", "learned", "graph", "cheb", "sparse"],
-                    help="dense: one N = 4096 cube solve per step (headline); batched: 4000 "
+                    help="dense: one N = 8192 cube solve per step (headline); batched: 4000 "
                          "parts of 64..768 orbitals per step; learned: predictor training "
                          "and evaluation; graph: graph-based divide and conquer of a chain; "
                          "cheb: finite-temperature Chebyshev expansion of the N = 4096 cube H; "
@@ -103,6 +114,8 @@ def parse_args():
                     help="cheb workload: chemical potential (eV) of the Fermi function")
     ap.add_argument("--cheb-beta", type=float, default=1.0,
                     help="cheb workload: inverse temperature (1/eV)")
+    ap.add_argument("--cheb-sites", type=int, default=1024,
+                    help="cheb workload: cube sites (x 4 orbitals)")
     ap.add_argument("--cheb-k", type=int, default=16)
     ap.add_argument("--cheb-m", type=int, default=16)
     ap.add_argument("--cheb-prec", default="fp32_split", choices=["fp32_split", "fp32_split_bf16"])
@@ -219,6 +232,11 @@ def cpu_cores():
 # reference arm: the CPU oracle as it stands
 
 def run_reference(args):
+    """The CPU oracle as it stands (plain FP64 SP2, numpy) on the host cores.
+    Each step is a bounded sample of one solve of the workload: the set-up
+    (bounds, X0 map, traces) and `k_sample` products. `ms_per_step` is the
+    measured time of one such step; `value` is solves/s, the sample's rate
+    scaled to a whole solve by its iteration count."""
     import numpy as np
     import oracle
     from workloads import cube_hamiltonian
@@ -232,23 +250,26 @@ def run_reference(args):
     w = np.linalg.eigvalsh(H)
     emin, emax = oracle.gershgorin_bounds(H)
     iters = oracle.spectral_sp2(w, nocc, args.tol, emin, emax)["iters"]
-    k_sample = 2
+    k_sample = 1 if n >= 6000 else 2
     for _ in range(args.warmup):
         time_oracle_products(H, nocc, 1)
-    times = []
+    step_sec, solve_sec = [], []
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         ts, tp = time_oracle_products(H, nocc, k_sample)
-        times.append(ts + iters * tp)
-    sec = statistics.mean(times)
+        step_sec.append(time.perf_counter() - t0)
+        solve_sec.append(ts + iters * tp)
+    sec = statistics.mean(solve_sec)
     value = 1.0 / sec
     sample = (f"{k_sample} of {iters} SP2 products (+ bounds and X0) per step on N={n}, "
-              f"scaled to a full solve by the iteration count")
+              f"scaled to a whole solve by the iteration count")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": statistics.mean(step_sec) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.sites, args.seed), "n": n,
                        "prec": "fp64 (numpy CPU oracle)", "tol": args.tol},
+            "solve_ms_extrapolated": sec * 1e3,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -668,7 +689,7 @@ def run_cheb(args):
     from workloads import cube_hamiltonian
     build()
     dev = torch.device("cuda", 0)
-    H_np, _ = cube_hamiltonian(args.sites, args.seed)
+    H_np, _ = cube_hamiltonian(args.cheb_sites, args.seed)
     n = H_np.shape[0]
     H = torch.from_numpy(H_np).to(dev)
     D = torch.empty_like(H)
@@ -740,7 +761,7 @@ def run_cheb(args):
                       else "bf16x3 split, f32 accumulate"),
             "data": "synthetic",
             "config": {"workload": f"Chebyshev Fermi operator (Paterson-Stockmeyer): random-cube "
-                                   f"tight-binding H, {args.sites} sites x 4 orbitals (N={n}), "
+                                   f"tight-binding H, {args.cheb_sites} sites x 4 orbitals (N={n}), "
                                    f"seed {args.seed}, mu={mu} eV, beta={beta}/eV, "
                                    f"L+1={k * m} terms (k={k}, m={m})",
                        "parallelism": "one GPU",
@@ -1114,9 +1135,38 @@ def main():
         line["e2e"] = {"value": world * K / (e2e_ms / 1e3), "unit": UNIT,
                        "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8}
 
+    # the same solve with bf16 hi+mid+lo split squarings (mixed runs with fp16)
+    D_bf16 = None
+    if args.prec == "mixed_fp16" and args.bf16_leg:
+        bopts = dict(opts, prec="mixed_bf16")
+        pkg.sp2_dense_ex(H, nocc, args.tol, D=D, **bopts)  # warm-up (builds its graph)
+        kb = min(K, 5)
+        bs, be = mk_events(kb), mk_events(kb)
+        torch.cuda.synchronize()
+        for i in range(kb):
+            flush.zero_()
+            bs[i].record(stream)
+            pkg.sp2_dense_ex(H, nocc, args.tol, D=D, info=False, **bopts)
+            be[i].record(stream)
+        torch.cuda.synchronize()
+        bms = sum(bs[i].elapsed_time(be[i]) for i in range(kb)) / kb
+        binfo = pkg.query()
+        D_bf16 = D.clone()
+        bchk = {}
+        if not args.no_check:
+            bchk = {"idempotency_max": float((D_bf16 @ D_bf16 - D_bf16).abs().max()),
+                    "trace_err": abs(float(torch.trace(D_bf16)) - nocc)}
+        line["mixed_bf16"] = {"value": 1e3 / bms, "unit": UNIT, "ms_per_step": bms,
+                              "steps": kb, "dtype": IMPL_DTYPE[impl] +
+                              " prefix/refine + bf16x3 split",
+                              "iters": binfo["iters"], "phase_iters": binfo["phase_iters"],
+                              "status": binfo["status"], "d_check": bchk}
+
     # plain FP64 SP2 on the same GPU (the comparison the metric asks for)
+    D_64 = None
     if args.prec != "fp64" and not args.no_fp64_baseline:
-        _, i64 = pkg.sp2_dense_ex(H, nocc, args.tol, D=D, prec="fp64")
+        if n < 6000:  # warm-up; at large n one solve takes tens of seconds and
+            pkg.sp2_dense_ex(H, nocc, args.tol, D=D, prec="fp64")  # its graph costs ~1 ms
         e0, e1 = mk_events(1)[0], mk_events(1)[0]
         torch.cuda.synchronize()
         flush.zero_()
@@ -1125,25 +1175,53 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1)
+        i64 = pkg.query()
+        D_64 = D.clone()
         line["fp64_baseline"] = {"value": 1e3 / t64, "unit": UNIT, "iters": i64["iters"],
+                                 "status": i64["status"],
                                  "speedup": (value / world) / (1e3 / t64)}
+        if "mixed_bf16" in line:
+            line["mixed_bf16"]["speedup_vs_fp64"] = line["mixed_bf16"]["value"] / (1e3 / t64)
 
     # CPU oracle on the host cores (rank 0, N = 1 only): one whole plain FP64
-    # SP2 solve (numpy), which is also the reference D for the error check
+    # SP2 solve (numpy), which is also the reference D of every error check
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
         ref = oracle.sp2_plain(H_np, nocc, args.tol)
         sec = time.perf_counter() - t0
-        err = float(np.abs(D_main.cpu().numpy() - ref["D"]).max())
+        Dref = ref["D"]
+        mixed_gate = {"max_abs_err": 1e-5, "trace_err": 1e-8}
+        gates = {"fp64": {"max_abs_err": 1e-10}, "df64": {"max_abs_err": 1e-10},
+                 "mixed_fp16": mixed_gate, "mixed_bf16": mixed_gate,
+                 "fp32_split": FP32_GATE, "fp32_split_bf16": FP32_GATE}
+        err = float(np.abs(D_main.cpu().numpy() - Dref).max())
         line["d_check"]["max_abs_err_vs_oracle"] = err
-        line["d_check"]["gate"] = 1e-10 if args.prec in ("fp64", "df64") else 1e-5
+        line["d_check"]["gate"] = gates[args.prec]
         line["d_check"]["oracle_iters"] = ref["iters"]
+        g = dict(gates[args.prec])
+        if "trace_err_per_n" in g:
+            g["trace_err"] = g.pop("trace_err_per_n") * n
+        line["d_check"]["gate"] = g
+        line["d_check"]["pass"] = bool(err <= g["max_abs_err"] and (
+            "trace_err" not in g or "trace_err" not in check or
+            check["trace_err"] <= g["trace_err"]))
+        if D_bf16 is not None:
+            e = float(np.abs(D_bf16.cpu().numpy() - Dref).max())
+            bc = line["mixed_bf16"]["d_check"]
+            bc["max_abs_err_vs_oracle"] = e
+            bc["gate"] = mixed_gate
+            bc["pass"] = bool(e <= 1e-5 and bc.get("trace_err", 0.0) <= 1e-8)
+        if D_64 is not None:
+            e = float(np.abs(D_64.cpu().numpy() - Dref).max())
+            line["fp64_baseline"]["d_check"] = {"max_abs_err_vs_oracle": e, "gate": 1e-10,
+                                                "pass": bool(e <= 1e-10)}
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": cpu_cores(),
                                 "kind": "oracle",
                                 "sample": f"one whole solve of the same N={n} workload "
                                           f"(plain FP64 SP2, numpy matmul, {ref['iters']} "
-                                          f"products)"}
+                                          f"products); its D is the reference of every "
+                                          f"error check in this line"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -104,7 +104,16 @@ typedef struct {
                            FP32_SPLIT_BF16 (else EINVAL); the product then skips every
                            128 x 128 block pair of X that holds no non-zero and leaves a
                            result tile that stays zero unwritten */
-  int32_t reserved[2];  /* must be zero */
+  int32_t wait_limit_us; /* bound on each pipeline wait (mbarrier) of the tensor-core product
+                           kernels, in microseconds; 0 (default) = 2 s. A wait that runs out
+                           ends the solve with PROGRESS_ETIMEOUT (D is then not valid): the
+                           kernel stops its loads and products, lets copies already in flight
+                           land and frees its tensor memory before it exits */
+  int32_t stall_test;   /* fault-injection test of those bounded waits: 0 (default) = off;
+                           1 = the first CTA of the first tensor-core product waits on a
+                           barrier that nothing arrives on, so the solve must end with
+                           PROGRESS_ETIMEOUT after wait_limit_us. Needs a mode with
+                           tensor-core products (not FP64 or DF64), else PROGRESS_EINVAL */
 } progress_opts_t;
 
 /* Result of one solve, read back from the device by the calls that take it. */
@@ -460,6 +469,80 @@ progress_status_t progress_mlp_train_step(int32_t in, int32_t hidden, int32_t ou
                                           const float* d_x, const float* d_target,
                                           const float* d_mask, float* d_scratch, float* d_loss,
                                           void* stream);
+
+/*
+ * Solve inputs of the learned sequence (a12) from the predictor's outputs,
+ * one row of `nout` floats per instance (device d_y [batch][nout]: u_min, u_max,
+ * then nout - 2 <= 256 branch logits), and the Gershgorin enclosure of each
+ * instance (device d_gersh [batch][2], §VIII.A), w = emax - emin:
+ *   d_bounds [batch][2] (device, written): emin + w max(u_min - margin, 0) and
+ *     emax - w max(u_max - margin, 0), each operation rounded on its own (no
+ *     fused multiply-add); an empty interval is replaced by the enclosure, so
+ *     the bounds never leave it;
+ *   d_bits [batch][4] (device, written, or NULL): branch k = bit k, 1 (2X - X^2)
+ *     iff logit k > 0;
+ *   d_len [batch] (device, written, or NULL): the number of leading logits with
+ *     |logit| >= logit_tau -- the predicted prefix; later branches are left to
+ *     the trace rule.
+ * These are the d_bounds, d_pred_bits, d_pred_len of progress_batch_ex_t.
+ * Asynchronous. Errors: EINVAL (batch < 0, nout outside [3, 258], margin < 0 or
+ * not finite, NULL pointer).
+ */
+progress_status_t progress_learned_inputs(int32_t batch, int32_t nout, const float* d_y,
+                                          const double* d_gersh, double margin, float logit_tau,
+                                          double* d_bounds, uint64_t* d_bits, int32_t* d_len,
+                                          void* stream);
+
+/*
+ * Training targets and masks of the predictor (device d_target, d_mask
+ * [batch][2 + kmax], written): targets 0 and 1 are d_ub[i * ld_ub + 0..1]
+ * (device float; the bound fractions of progress_learned_labels, or the
+ * predictor's own outputs when later training must keep its bounds), mask 1;
+ * targets 2 + k are bit k of d_bits [batch][4] (device, or NULL = 0), masked
+ * (0) for k >= d_iters[i] (device, or NULL = 0) and for every k when
+ * d_reject[i] != 0 (device, or NULL: none rejected). 1 <= kmax <= 256.
+ * Asynchronous. Errors: EINVAL.
+ */
+progress_status_t progress_learned_targets(int32_t batch, int32_t kmax, const float* d_ub,
+                                           int32_t ld_ub, const uint64_t* d_bits,
+                                           const int32_t* d_iters, const int32_t* d_reject,
+                                           float* d_target, float* d_mask, void* stream);
+
+/*
+ * Bound labels of the predictor from SP2 runs of this library: the projector D1
+ * onto the lowest state of H (a batched solve with nocc = 1, bf16 hi+mid+lo
+ * split products) gives eps_1 = Tr(H D1), the projector onto the lowest state
+ * of -H gives eps_N = Tr(H D1'); then u_min = max((eps_1 - emin)/w, 0) and
+ * u_max = max((emax - eps_N)/w, 0) with the Gershgorin enclosure [emin, emax],
+ * w = emax - emin.
+ *   h_n, h_offset  HOST [batch]: the batch layout (as progress_sp2_batched)
+ *   d_n, d_offset  DEVICE [batch]: the same layout
+ *   dH             device, packed FP64 instances, read only
+ *   d_u            device float [batch][2], written: u_min, u_max
+ *   d_gersh        device double [batch][2], written: emin, emax
+ *   d_eps          device double [2][batch], written (eps_1 then eps_N), or NULL
+ * Allocates and frees its own work space (two packed copies) and synchronizes
+ * the stream. Errors: EINVAL, ENOMEM/ECUDA, and those of progress_sp2_batched.
+ */
+progress_status_t progress_learned_labels(int32_t batch, const int32_t* h_n,
+                                          const int64_t* h_offset, const int32_t* d_n,
+                                          const int64_t* d_offset, const double* dH, double tol,
+                                          float* d_u, double* d_gersh, double* d_eps,
+                                          void* stream);
+
+/*
+ * Safety margin of the predicted bounds, calibrated on held-out instances:
+ * with predictions d_y and targets d_t (device float, rows of ld_y / ld_t, the
+ * first two entries of a row are the bound fractions), the overshoot of
+ * instance i is max(y_i0 - t_i0, y_i1 - t_i1, 0); *margin_out (host) = the
+ * `quantile` of the overshoots (linear interpolation between order
+ * statistics), at least `floor`. A bound that cuts the spectrum makes the judge
+ * reject the run, so the quantile sets the expected fallback rate of that
+ * cause. Synchronizes the stream. Errors: EINVAL.
+ */
+progress_status_t progress_learned_margin(int32_t batch, const float* d_y, int32_t ld_y,
+                                          const float* d_t, int32_t ld_t, double quantile,
+                                          double floor, double* margin_out, void* stream);
 
 /* Synchronize `stream` and report the last solve queued on it. */
 progress_status_t progress_sp2_query(void* stream, progress_info_t* info);

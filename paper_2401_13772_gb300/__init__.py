@@ -64,7 +64,8 @@ def gershgorin_bounds(H, out=None, stream=None):
 
 
 def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None, emax=None,
-              loop_mode=0, loop_events=None, slice_fixed=0, fp64_impl=0, tau=0.0):
+              loop_mode=0, loop_events=None, slice_fixed=0, fp64_impl=0, tau=0.0,
+              wait_limit_us=0, stall_test=0):
     o = Opts()
     load().progress_opts_default(ctypes.byref(o))
     o.prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
@@ -77,6 +78,8 @@ def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None
     o.slice_fixed = int(slice_fixed)
     o.fp64_impl = int(fp64_impl)
     o.tau = float(tau)
+    o.wait_limit_us = int(wait_limit_us)
+    o.stall_test = int(stall_test)
     if loop_events is not None:
         # torch.cuda.Event pair, already created (recorded once)
         o.loop_events[0] = loop_events[0].cuda_event
@@ -100,8 +103,8 @@ def sp2_dense(H, nocc, tol, D=None, stream=None):
 
 def sp2_dense_ex(H, nocc, tol, D=None, info=True, stream=None, raise_on_status=True, **opts):
     """SP2 solve with options (prec, rule, fp64_prefix, maxiter, emin, emax,
-    loop_mode, loop_events, slice_fixed, fp64_impl, tau). With info=True it
-    synchronizes and returns (D, info dict)."""
+    loop_mode, loop_events, slice_fixed, fp64_impl, tau, wait_limit_us,
+    stall_test). With info=True it synchronizes and returns (D, info dict)."""
     import torch
     _check_matrix(H, "H")
     if D is None:
@@ -115,7 +118,8 @@ def sp2_dense_ex(H, nocc, tol, D=None, info=True, stream=None, raise_on_status=T
                                           ctypes.byref(o),
                                           ctypes.byref(inf) if info else None,
                                           _stream_ptr(stream))
-    if st != _lib.OK and (raise_on_status or st not in (_lib.ENOCONV, _lib.EBOUNDS)):
+    if st != _lib.OK and (raise_on_status or
+                          st not in (_lib.ENOCONV, _lib.EBOUNDS, _lib.ETIMEOUT)):
         check(st)
     if info:
         return D, inf.to_dict()
@@ -342,6 +346,15 @@ def cheb_choose_km(terms, mu, beta, emin, emax, max_growth=8.0):
         raise ValueError("no (k, m) with k m >= terms keeps the growth within max_growth")
     return {"k": best[1], "m": best[2], "products": best[0][0], "terms": best[0][1],
             "growth": best[3]}
+
+
+def query(stream=None):
+    """Synchronize the stream and return the info dict of the last solve queued on it."""
+    inf = _lib.Info()
+    st = load().progress_sp2_query(_stream_ptr(stream), ctypes.byref(inf))
+    if st not in (_lib.OK, _lib.ENOCONV, _lib.EBOUNDS, _lib.ETIMEOUT):
+        check(st)
+    return inf.to_dict()
 
 
 def history(stream=None, cap=256):

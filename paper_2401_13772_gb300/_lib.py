@@ -27,7 +27,8 @@ class Opts(ctypes.Structure):
                 ("emin", ctypes.c_double), ("emax", ctypes.c_double),
                 ("loop_mode", ctypes.c_int32), ("slice_fixed", ctypes.c_int32),
                 ("loop_events", ctypes.c_void_p * 2), ("fp64_impl", ctypes.c_int32),
-                ("tau", ctypes.c_float), ("reserved", ctypes.c_int32 * 2)]
+                ("tau", ctypes.c_float), ("wait_limit_us", ctypes.c_int32),
+                ("stall_test", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -118,6 +119,14 @@ SIGNATURES = {
     "progress_cheb_plan": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _D, _D, _D, _D,
                                           ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
     "progress_features": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P]),
+    "progress_learned_inputs": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _D,
+                                               ctypes.c_float, _P, _P, _P, _P]),
+    "progress_learned_targets": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P,
+                                                ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
+    "progress_learned_labels": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _D, _P, _P,
+                                               _P, _P]),
+    "progress_learned_margin": (ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_int32, _P,
+                                               ctypes.c_int32, _D, _D, _P, _P]),
     "progress_trace_hd": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
     "progress_mlp_param_count": (ctypes.c_int32, [ctypes.c_int32] * 3),
     "progress_mlp_scratch_floats": (ctypes.c_int64, [ctypes.c_int32] * 4),

@@ -290,8 +290,10 @@ progress_status_t query(Workspace* w, progress_info_t* info) {
   CK(cudaStreamSynchronize(w->stream), "cudaStreamSynchronize");
   fill_info(*w->h_state, info);
   if (w->h_state->status != PROGRESS_OK) {
-    g_err = w->h_state->status == PROGRESS_ENOCONV ? "SP2 did not converge within maxiter"
-                                                   : "SP2 iterate left [0,1] (bad bounds or input)";
+    const int s = w->h_state->status;
+    g_err = s == PROGRESS_ENOCONV   ? "SP2 did not converge within maxiter"
+            : s == PROGRESS_ETIMEOUT ? "a bounded device-side wait gave up (D is not valid)"
+                                     : "SP2 iterate left [0,1] (bad bounds or input)";
     return (progress_status_t)w->h_state->status;
   }
   return PROGRESS_OK;
@@ -379,6 +381,10 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   if (o.loop_mode != 0 && o.loop_mode != 1) return fail(PROGRESS_EINVAL, "loop_mode must be 0 or 1");
   if (o.slice_fixed != 0 && o.slice_fixed != 1) return fail(PROGRESS_EINVAL, "slice_fixed must be 0 or 1");
   if (!(o.tau >= 0.0f) || !isfinite(o.tau)) return fail(PROGRESS_EINVAL, "tau must be finite and >= 0");
+  if (o.wait_limit_us < 0) return fail(PROGRESS_EINVAL, "wait_limit_us must be >= 0");
+  if (o.stall_test != 0 && o.stall_test != 1) return fail(PROGRESS_EINVAL, "stall_test must be 0 or 1");
+  if (o.stall_test && (o.prec == PROGRESS_FP64 || o.prec == PROGRESS_DF64))
+    return fail(PROGRESS_EINVAL, "stall_test needs a mode with tensor-core products");
   if (o.tau > 0.0f && (o.prec != PROGRESS_FP32_SPLIT || o.slice_fixed))
     return fail(PROGRESS_EINVAL,
                 "tau > 0 needs prec FP32_SPLIT or FP32_SPLIT_BF16 with floating slices");
@@ -431,6 +437,9 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   p.emin_override = o.emin;
   p.emax_override = o.emax;
   p.tau = o.tau;
+  p.wait_ns = o.wait_limit_us > 0 ? 1000ull * (unsigned long long)o.wait_limit_us
+                                  : 2000000000ull;
+  p.stall_test = o.stall_test;
 
   CK(sp2::launch_init(w->buf, p, s), "init launch");
   CK(sp2::launch_gershgorin(dH, n, w->buf, nullptr, s), "gershgorin launch");

@@ -57,6 +57,9 @@ struct State {
   double judge_delta;
   double y_mu;  // PROGRESS_RULE_MU: the chemical potential under the same map as X_k
   unsigned long long kblocks;  // thresholded SP2: 64-wide k-blocks streamed (all products)
+  unsigned long long wait_ns;  // bound on each pipeline wait of the tensor-core kernels
+  int stall_test;              // 1: CTA 0 of a tensor-core product waits on a barrier that
+                               // nothing arrives on (test of the bounded waits)
   unsigned long long bits[4];
   double idem_hist[kMaxHist];
   double margin_hist[kMaxHist];

@@ -35,6 +35,8 @@ __global__ void init_kernel(State* st, SolveParams p) {
     st->emin_override = p.emin_override;
     st->emax_override = p.emax_override;
     st->best_split_idem = INFINITY;
+    st->wait_ns = p.wait_ns;
+    st->stall_test = p.stall_test;
     st->phase = (p.prec == PROGRESS_FP32_SPLIT) ? kPhaseSplit : kPhaseFP64;
   }
 }

@@ -35,6 +35,8 @@ struct SolveParams {
   double tol;
   double emin_override, emax_override;
   float tau;  // thresholded SP2 cutoff (0 = dense)
+  unsigned long long wait_ns;  // bound on each pipeline wait of the tensor-core kernels
+  int stall_test;              // test of the bounded waits (see progress_opts_t)
 };
 
 cudaError_t launch_init(const DevBuffers& b, const SolveParams& p, cudaStream_t s);

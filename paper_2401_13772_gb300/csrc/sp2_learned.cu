@@ -239,9 +239,132 @@ __global__ void sum_kernel(const float* __restrict__ x, int count, float* __rest
   if (threadIdx.x == 0) *out = (float)acc;
 }
 
+// ---------------------------------------------------------------------------
+// Solve inputs from the predictor's outputs, one thread per instance:
+//   bounds: u_min, u_max (outputs 0, 1; fractions of the Gershgorin width w)
+//           widened by `margin`, emin' = emin + w max(u_min - margin, 0),
+//           emax' = emax - w max(u_max - margin, 0); an empty interval falls
+//           back to the Gershgorin enclosure, so the result never leaves it;
+//   bits:   branch k is 1 (2X - X^2) iff logit k > 0;
+//   len:    the number of leading logits with |logit| >= tau (only that
+//           prefix of the sequence is predicted; later branches are left to
+//           the trace rule).
+// The products and sums are rounded one operation at a time (no FMA), as in a
+// plain FP64 evaluation of the formulas.
+__global__ void predict_inputs_kernel(int batch, int nout, const float* __restrict__ Y,
+                                      const double* __restrict__ gersh, double margin, float tau,
+                                      int kmax, double* __restrict__ bounds,
+                                      unsigned long long* __restrict__ bits,
+                                      int32_t* __restrict__ len) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= batch) return;
+  const float* y = Y + (size_t)i * nout;
+  const double emin = gersh[2 * i], emax = gersh[2 * i + 1];
+  const double w = __dsub_rn(emax, emin);
+  const double u0 = fmax(__dsub_rn((double)y[0], margin), 0.0);
+  const double u1 = fmax(__dsub_rn((double)y[1], margin), 0.0);
+  double lo = __dadd_rn(emin, __dmul_rn(w, u0));
+  double hi = __dsub_rn(emax, __dmul_rn(w, u1));
+  if (!(hi > lo)) {
+    lo = emin;
+    hi = emax;
+  }
+  bounds[2 * i] = lo;
+  bounds[2 * i + 1] = hi;
+  if (bits) {
+    unsigned long long wd[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int k = 0; k < kmax; ++k)
+      if (y[kBounds + k] > 0.0f) wd[k >> 6] |= 1ull << (k & 63);
+    for (int q = 0; q < 4; ++q) bits[4 * i + q] = wd[q];
+  }
+  if (len) {
+    int L = 0;
+    while (L < kmax && fabsf(y[kBounds + L]) >= tau) ++L;
+    len[i] = L;
+  }
+}
+
+// Training targets and masks, one thread per instance: the two bound targets
+// (ub[i * ld_ub + 0..1]), then the branch bits of a labelled SP2 run, masked
+// beyond its product count and for runs that fell back (reject[i] != 0).
+__global__ void targets_kernel(int batch, int kmax, const float* __restrict__ ub, int ld_ub,
+                               const unsigned long long* __restrict__ bits,
+                               const int32_t* __restrict__ iters,
+                               const int32_t* __restrict__ reject, float* __restrict__ T,
+                               float* __restrict__ M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= batch) return;
+  const int nout = kBounds + kmax;
+  float* t = T + (size_t)i * nout;
+  float* m = M + (size_t)i * nout;
+  t[0] = ub[(size_t)i * ld_ub];
+  t[1] = ub[(size_t)i * ld_ub + 1];
+  m[0] = 1.0f;
+  m[1] = 1.0f;
+  const int it = iters ? iters[i] : 0;
+  const bool ok = !(reject && reject[i]);
+  for (int k = 0; k < kmax; ++k) {
+    t[kBounds + k] = bits ? (float)((bits[4 * i + (k >> 6)] >> (k & 63)) & 1ull) : 0.0f;
+    m[kBounds + k] = (ok && k < it) ? 1.0f : 0.0f;
+  }
+}
+
+// Bound targets from the extremal eigenvalues: u_min = max((eps_1 - emin)/w, 0),
+// u_max = max((emax - eps_N)/w, 0), w = emax - emin (the Gershgorin enclosure).
+__global__ void bound_fractions_kernel(int batch, const double* __restrict__ eps1,
+                                       const double* __restrict__ epsN,
+                                       const double* __restrict__ gersh,
+                                       float* __restrict__ u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= batch) return;
+  const double emin = gersh[2 * i], emax = gersh[2 * i + 1];
+  const double w = emax - emin;
+  u[2 * i] = (float)fmax((eps1[i] - emin) / w, 0.0);
+  u[2 * i + 1] = (float)fmax((emax - epsN[i]) / w, 0.0);
+}
+
+// y = -x over `count` doubles (the operator -H whose lowest state is H's highest).
+__global__ void negate_kernel(const double* __restrict__ x, int64_t count, double* __restrict__ y) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+       q += (int64_t)gridDim.x * blockDim.x)
+    y[q] = -x[q];
+}
+
 inline int blocks(int64_t work) { return (int)((work + kThreads - 1) / kThreads); }
 
 }  // namespace
+
+cudaError_t predict_inputs(int batch, int nout, const float* d_y, const double* d_gersh,
+                           double margin, float tau, double* d_bounds, uint64_t* d_bits,
+                           int32_t* d_len, cudaStream_t s) {
+  predict_inputs_kernel<<<blocks(batch), kThreads, 0, s>>>(
+      batch, nout, d_y, d_gersh, margin, tau, nout - kBounds, d_bounds,
+      reinterpret_cast<unsigned long long*>(d_bits), d_len);
+  return cudaGetLastError();
+}
+
+cudaError_t targets(int batch, int kmax, const float* d_ub, int ld_ub, const uint64_t* d_bits,
+                    const int32_t* d_iters, const int32_t* d_reject, float* d_t, float* d_m,
+                    cudaStream_t s) {
+  targets_kernel<<<blocks(batch), kThreads, 0, s>>>(
+      batch, kmax, d_ub, ld_ub, reinterpret_cast<const unsigned long long*>(d_bits), d_iters,
+      d_reject, d_t, d_m);
+  return cudaGetLastError();
+}
+
+cudaError_t bound_fractions(int batch, const double* d_eps1, const double* d_epsN,
+                            const double* d_gersh, float* d_u, cudaStream_t s) {
+  bound_fractions_kernel<<<blocks(batch), kThreads, 0, s>>>(batch, d_eps1, d_epsN, d_gersh, d_u);
+  return cudaGetLastError();
+}
+
+cudaError_t negate(const double* d_x, int64_t count, double* d_y, cudaStream_t s) {
+  int64_t b = (count + kThreads - 1) / kThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  negate_kernel<<<(int)b, kThreads, 0, s>>>(d_x, count, d_y);
+  return cudaGetLastError();
+}
 
 int param_count(int in, int hid, int out) { return Layout{in, hid, out}.count(); }
 

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __shared__ int s_consumed;
   __shared__ int s_last;
   __shared__ double s_scratch[2 * THREADS / 32];
-  __shared__ __align__(8) uint64_t s_bars[2 * STAGES + 3];
+  __shared__ __align__(8) uint64_t s_bars[2 * STAGES + 4];
 
   State* st = buf.st;
   const int done = __ldcg(&st->done);
@@ -204,6 +204,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int bit = __ldcg(&st->bit);
   const int ld = st->ld;
   const int prec = st->prec;
+  const uint64_t wlim = __ldcg(&st->wait_ns);  // bound on the pipeline waits
+  const bool stall = __ldcg(&st->stall_test) != 0 && blockIdx.x == 0;
   const bool want_slices =
       (prec == PROGRESS_MIXED_FP16 || prec == PROGRESS_MIXED_BF16) && phase == kPhaseFP64 &&
       (k_iter + 1 >= st->fp64_prefix);
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t g2full = bars + 8u * (2 * STAGES);
   const uint32_t g2empty = bars + 8u * (2 * STAGES + 1);
   const uint32_t accum_bar = bars + 8u * (2 * STAGES + 2);
+  const uint32_t stall_bar = bars + 8u * (2 * STAGES + 3);  // nothing arrives on it
 
   if (threadIdx.x == 0) {
     s_err = 0;
@@ -234,6 +237,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     mbar_init(g2full, 1);
     mbar_init(g2empty, NEPI);
     mbar_init(accum_bar, 1);
+    mbar_init(stall_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int kb = 0; kb < KB; ++kb, ++issued) {
         const int s = kb % STAGES;
         const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        if (!mbar_wait(empty_bar(s), ph ^ 1u, err)) break;
+        if (!mbar_wait(empty_bar(s), ph ^ 1u, err, true, wlim)) break;
         mbar_expect_tx(full_bar(s), stage_bytes);
         const uint32_t sa = base + s * STAGE_BYTES;
 #pragma unroll
@@ -276,7 +280,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool chunk_last = (kb % CHUNK_KB) == CHUNK_KB - 1 || kb == KB - 1;
         const int s = kb % STAGES;
         const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        if (!mbar_wait(full_bar(s), ph, err)) {
+        // test of the bounded waits: after the first k-block's products, wait
+        // on a barrier that nothing arrives on; it runs out after wlim
+        if (stall && kb == 1 && !mbar_wait(stall_bar, 0u, err, true, wlim)) {
+          ok = false;
+          break;
+        }
+        if (!mbar_wait(full_bar(s), ph, err, true, wlim)) {
           ok = false;
           break;
         }
@@ -326,7 +336,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (chunk_first) {
           issue_rest();
           if (c > 0) {  // the drain has read G2 of the previous chunk
-            if (!mbar_wait(g2empty, (uint32_t)(c - 1) & 1u, err)) {
+            if (!mbar_wait(g2empty, (uint32_t)(c - 1) & 1u, err, true, wlim)) {
               ok = false;
               break;
             }
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   for (int j = 0; j < 64; ++j) g2acc[j] = 0;
   if (epi) {
     for (int c = 0; c < NC; ++c) {
-      if (!mbar_wait(g2full, (uint32_t)c & 1u, err)) break;
+      if (!mbar_wait(g2full, (uint32_t)c & 1u, err, true, wlim)) break;
       tc_fence_after();
       uint32_t v[64];
 #pragma unroll

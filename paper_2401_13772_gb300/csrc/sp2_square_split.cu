@@ -113,6 +113,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int k_iter = __ldcg(&st->iter);
   const int bit = __ldcg(&st->bit);
   const int ld = st->ld;
+  const uint64_t wlim = __ldcg(&st->wait_ns);  // bound on the pipeline waits
+  const bool stall = __ldcg(&st->stall_test) != 0 && blockIdx.x == 0;
   // FP64 X' is needed if the schedule may switch to FP64 refinement after
   // this product (MIXED: the split phase has stalled once already).
   const bool want_fp64 = (st->prec == PROGRESS_MIXED_FP16 || st->prec == PROGRESS_MIXED_BF16) &&
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const uint32_t chunk_full = bars + 8u * (2 * C::STAGES + 1);              // [NBUF]
   const uint32_t chunk_empty = bars + 8u * (2 * C::STAGES + 1 + C::NBUF);   // [NBUF]
+  const uint32_t stall_bar = bars + 8u * (2 * C::STAGES + 1 + 2 * C::NBUF); // never arrived
 
   if (threadIdx.x == 0) {
     s_err = 0;
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(chunk_full + 8u * b, 1);
       mbar_init(chunk_empty + 8u * b, DRAIN_WARPS);
     }
+    mbar_init(stall_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int kb = 0; kb < KB; ++kb, ++issued) {
         const int s = kb % C::STAGES;
         const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-        if (!mbar_wait(empty_bar(s), ph ^ 1u, err)) break;
+        if (!mbar_wait(empty_bar(s), ph ^ 1u, err, true, wlim)) break;
         mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
         const uint32_t sa = base + s * C::STAGE_BYTES;
 #pragma unroll
@@ -192,7 +196,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool chunk_last = (kb % CHUNK) == CHUNK - 1 || kb == KB - 1;
         const uint32_t acc0 = tmem + 128u * cb;
         if (chunk_first) {
-          if (!mbar_wait(chunk_empty + 8u * cb, ((uint32_t)(c / C::NBUF) & 1u) ^ 1u, err)) {
+          if (!mbar_wait(chunk_empty + 8u * cb, ((uint32_t)(c / C::NBUF) & 1u) ^ 1u, err, true,
+                         wlim)) {
             ok = false;
             break;
           }
@@ -200,7 +205,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         const int s = kb % C::STAGES;
         const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-        if (!mbar_wait(full_bar(s), ph, err)) {
+        // test of the bounded waits: after the first k-block's products, wait
+        // on a barrier that nothing arrives on; it runs out after wlim
+        if (stall && kb == 1 && !mbar_wait(stall_bar, 0u, err, true, wlim)) {
+          ok = false;
+          break;
+        }
+        if (!mbar_wait(full_bar(s), ph, err, true, wlim)) {
           ok = false;
           break;
         }
@@ -249,7 +260,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (drain) {
     for (int c = 0; c < NC; ++c) {
       const int cb = c % C::NBUF;
-      if (!mbar_wait(chunk_full + 8u * cb, (uint32_t)(c / C::NBUF) & 1u, err)) break;
+      if (!mbar_wait(chunk_full + 8u * cb, (uint32_t)(c / C::NBUF) & 1u, err, true, wlim)) break;
       tc_fence_after();
       float v[DCOLS];
 #pragma unroll

@@ -3,9 +3,11 @@ it times (default options: mixed FP16 schedule with digit-product prefix and
 refinement; batched launch configuration from the autotuner).
 
 N = 4096 (1024-site cube): the whole D against the oracle's plain FP64 SP2,
-element by element (about 20 s of numpy on the host). N = 8192 (2048 sites):
-properties that hold at any size, on sampled rows -- symmetry, Tr D = Nocc,
-D^2 = D and [H, D] = 0 -- with the exact gate on Tr D. 4000 batched parts:
+element by element (about 20 s of numpy on the host), for the mixed schedule
+(gate 1e-5), plain FP64 (gate 1e-10) and the FP32-class all-split modes.
+N = 8192 (2048 sites, the benchmark's headline): the whole D of the mixed FP16
+and mixed BF16 schedules against one oracle solve (gates max |D - D_ref| <=
+1e-5, |Tr D - Nocc| <= 1e-8), plus the invariants on sampled rows. 4000 batched parts:
 the autotuned launch, then 40 parts sampled across the size range, each
 against the oracle's plain FP64 SP2. The Chebyshev workload (N = 4096, L + 1 =
 256): the whole D against the oracle's evaluation of the same expansion. The
@@ -33,38 +35,101 @@ def pkg():
     return p
 
 
-def bench_solve(pkg, sites):
+def solve(pkg, H, nocc, **opts):
     import torch
-    H, nocc = cube_hamiltonian(sites, 0)
     Hd = torch.from_numpy(H).to("cuda:0")
-    D, info = pkg.sp2_dense_ex(Hd, nocc, 1e-10, prec="mixed_fp16", fp64_prefix=8)
+    D, info = pkg.sp2_dense_ex(Hd, nocc, 1e-10, **opts)
     torch.cuda.synchronize()
-    return H, nocc, D.cpu().numpy(), info
+    return D.cpu().numpy(), info
 
 
-def test_n4096_mixed_matches_oracle_elementwise(pkg):
-    H, nocc, D, info = bench_solve(pkg, 1024)
-    assert info["status"] == "OK" and info["converged"]
+@pytest.fixture(scope="module")
+def cube4096():
+    """N = 4096 cube (1024 sites, seed 0) and one whole oracle solve of it
+    (plain FP64 SP2, about 20 s of numpy on the host)."""
+    H, nocc = cube_hamiltonian(1024, 0)
     ref = oracle.sp2_plain(H, nocc, 1e-10)
     assert ref["converged"]
+    return H, nocc, ref
+
+
+@pytest.fixture(scope="module")
+def cube8192():
+    """N = 8192 cube (2048 sites, seed 0) and one whole oracle solve of it
+    (plain FP64 SP2, a few minutes of numpy on the host)."""
+    H, nocc = cube_hamiltonian(2048, 0)
+    ref = oracle.sp2_plain(H, nocc, 1e-10)
+    assert ref["converged"]
+    return H, nocc, ref
+
+
+MIXED = dict(fp64_prefix=8)  # the benchmark's schedule: 8 FP64-accurate products first
+
+
+def test_n4096_mixed_matches_oracle_elementwise(pkg, cube4096):
+    H, nocc, ref = cube4096
+    D, info = solve(pkg, H, nocc, prec="mixed_fp16", **MIXED)
+    assert info["status"] == "OK" and info["converged"]
     err = float(np.abs(D - ref["D"]).max())
     assert err <= 1e-5, err                      # mixed-path gate
     assert abs(np.trace(D) - nocc) <= 1e-8
     assert np.array_equal(D, D.T)
 
 
-def test_n8192_mixed_properties_on_sampled_rows(pkg):
-    H, nocc, D, info = bench_solve(pkg, 2048)
+def test_n4096_fp64_matches_oracle_elementwise(pkg, cube4096):
+    # plain FP64 SP2 (native FP64 products) at the N = 4096 size: FP64 gate
+    H, nocc, ref = cube4096
+    D, info = solve(pkg, H, nocc, prec="fp64")
+    assert info["status"] == "OK" and info["converged"]
+    assert abs(info["iters"] - ref["iters"]) <= 1
+    err = float(np.abs(D - ref["D"]).max())
+    assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("prec", ["fp32_split", "fp32_split_bf16"])
+def test_n4096_fp32_split_matches_oracle_elementwise(pkg, cube4096, prec):
+    # every product in FP32-class split precision, no FP64 refinement. Gate
+    # (FP32-class reading): max |D - D_ref| <= 1e-4 and |Tr D - Nocc| <= 4 n 2^-22
+    # -- the split phase stops on its round-off floor, where the idempotency
+    # error, and with it the trace error, is of order n times the slices'
+    # 2^-22 resolution (measured: 2.4e-5 and 1.5e-3 at N = 4096)
+    H, nocc, ref = cube4096
+    n = H.shape[0]
+    D, info = solve(pkg, H, nocc, prec=prec)
+    assert info["status"] == "OK" and info["converged"]
+    err = float(np.abs(D - ref["D"]).max())
+    tr = abs(np.trace(D) - nocc)
+    print(f"{prec}: max|D - D_ref| = {err:.3e}, |Tr D - Nocc| = {tr:.3e}")
+    assert err <= 1e-4, err
+    assert tr <= 4.0 * n * 2.0 ** -22, tr
+
+
+@pytest.mark.parametrize("prec", ["mixed_fp16", "mixed_bf16"])
+def test_n8192_mixed_matches_oracle_elementwise(pkg, cube8192, prec):
+    # the benchmark's headline workload: the whole D against the oracle's
+    H, nocc, ref = cube8192
+    D, info = solve(pkg, H, nocc, prec=prec, **MIXED)
+    assert info["status"] == "OK" and info["converged"], info
+    err = float(np.abs(D - ref["D"]).max())
+    tr = abs(np.trace(D) - nocc)
+    print(f"{prec} N=8192: max|D - D_ref| = {err:.3e}, |Tr D - Nocc| = {tr:.3e}, "
+          f"phases {info['phase_iters']}")
+    assert err <= 1e-5, err
+    assert tr <= 1e-8, tr
+    assert np.array_equal(D, D.T)
+
+
+def test_n8192_mixed_properties_on_sampled_rows(pkg, cube8192):
+    # smoke check of the invariants that hold at any size (not a parity test)
+    H, nocc, _ = cube8192
+    D, info = solve(pkg, H, nocc, prec="mixed_fp16", **MIXED)
     assert info["status"] == "OK" and info["converged"]
     n = H.shape[0]
-    assert np.array_equal(D, D.T)
-    assert abs(np.trace(D) - nocc) <= 1e-8
     rows = np.random.default_rng(0).choice(n, size=64, replace=False)
     idem = float(np.abs(D[rows] @ D - D[rows]).max())
     comm = float(np.abs(H[rows] @ D - D[rows] @ H).max()) / float(np.abs(H).max())
     assert idem <= 1e-9, idem
     assert comm <= 1e-4, comm
-    # the spectrum of the sampled principal block stays inside [0, 1]
     w = np.linalg.eigvalsh(D[np.ix_(rows, rows)])
     assert w.min() >= -1e-9 and w.max() <= 1.0 + 1e-9
 
