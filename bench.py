@@ -515,8 +515,7 @@ def run_learned(args):
     for mg in sorted({round(margin, 4), 0.03, 0.05, 0.08}):
         if mg < margin:
             continue
-        r = L.batched_solve(vb, vnocc, bounds=L.predicted_bounds(
-            vY, vplain["bounds"][:, 0], vplain["bounds"][:, 1], mg))
+        r = L.batched_solve(vb, vnocc, bounds=L.predicted_bounds(vY, vplain["bounds"], mg))
         sweep[mg] = (r["products"].double().mean().item(), r["fallback"].double().mean().item())
     margin_cal = margin
     margin = min(sweep, key=lambda k: (sweep[k][0], k))
@@ -537,13 +536,13 @@ def run_learned(args):
         return out, e0.elapsed_time(e1) / 1e3
 
     plain, t_plain = timed(lambda: L.batched_solve(ev, nocc))
-    g0, g1 = plain["bounds"][:, 0], plain["bounds"][:, 1]
+    gersh = plain["bounds"]
 
     def learned_solve():
         Y = P.predict(L.features(ev))
-        return L.batched_solve(ev, nocc, bounds=L.predicted_bounds(Y, g0, g1, margin))
+        return L.batched_solve(ev, nocc, bounds=L.predicted_bounds(Y, gersh, margin))
     lb, t_lb = timed(learned_solve)
-    lj, t_lj = timed(lambda: L.solve_learned(P, ev, nocc, g0, g1, margin, judge_delta=0.5))
+    lj, t_lj = timed(lambda: L.solve_learned(P, ev, nocc, gersh, margin, judge_delta=0.5))
     line = {"metric": METRIC, "value": args.eval_count / t_lb, "unit": UNIT, "n_gpus": 1,
             "steps": 1, "warmup": 1, "ms_per_step": t_lb * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 split, f32 accumulate",

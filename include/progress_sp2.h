@@ -423,6 +423,21 @@ progress_status_t progress_cheb_plan(int32_t k, int32_t m, double mu, double bet
                                      double* dcoef, double* inv_s, double* ab, int32_t* counts);
 
 /*
+ * Choice of the Paterson-Stockmeyer split for progress_cheb_fermi (host only,
+ * no GPU): among the splits k m >= terms (k = 1..64, m = ceil(terms / k) <= 64)
+ * whose nested sums stay bounded -- the plan's growth sum_ij |d_ij| <=
+ * max_growth, since a large growth multiplies the products' rounding error --
+ * the one whose plan (progress_cheb_plan) has the fewest matrix products, ties
+ * to fewer terms. Writes k, m and (if not NULL) the product count and growth.
+ * Errors: EINVAL (terms outside [1, 4096], bad mu, beta or bounds, max_growth
+ * <= 0, no split qualifies).
+ */
+progress_status_t progress_cheb_choose(int32_t terms, double mu, double beta, double emin,
+                                       double emax, double max_growth, int32_t* k_out,
+                                       int32_t* m_out, int32_t* products_out,
+                                       double* growth_out);
+
+/*
  * Features of the learned predictor, 37 floats per instance (device output
  * [batch][37]): Gershgorin emin/w, emax/w (w = emax - emin, §VIII.A),
  * Tr H/(n w), ||H||_F/(sqrt(n) w), a 32-bin histogram of diag(H) over
@@ -531,18 +546,18 @@ progress_status_t progress_learned_labels(int32_t batch, const int32_t* h_n,
                                           void* stream);
 
 /*
- * Safety margin of the predicted bounds, calibrated on held-out instances:
- * with predictions d_y and targets d_t (device float, rows of ld_y / ld_t, the
- * first two entries of a row are the bound fractions), the overshoot of
- * instance i is max(y_i0 - t_i0, y_i1 - t_i1, 0); *margin_out (host) = the
- * `quantile` of the overshoots (linear interpolation between order
- * statistics), at least `floor`. A bound that cuts the spectrum makes the judge
- * reject the run, so the quantile sets the expected fallback rate of that
- * cause. Synchronizes the stream. Errors: EINVAL.
+ * Safety margin of the predicted bounds, calibrated on held-out instances
+ * (host computation, no GPU): with predictions h_y and targets h_t (HOST
+ * float arrays, rows of ld_y / ld_t entries whose first two are the bound
+ * fractions), the overshoot of instance i is max(y_i0 - t_i0, y_i1 - t_i1, 0);
+ * *margin_out = the `quantile` of the overshoots (linear interpolation
+ * between order statistics), at least `floor`. A bound that cuts the spectrum
+ * makes the judge reject the run, so the quantile sets the expected fallback
+ * rate of that cause. Errors: EINVAL.
  */
-progress_status_t progress_learned_margin(int32_t batch, const float* d_y, int32_t ld_y,
-                                          const float* d_t, int32_t ld_t, double quantile,
-                                          double floor, double* margin_out, void* stream);
+progress_status_t progress_learned_margin(int32_t batch, const float* h_y, int32_t ld_y,
+                                          const float* h_t, int32_t ld_t, double quantile,
+                                          double floor, double* margin_out);
 
 /* Synchronize `stream` and report the last solve queued on it. */
 progress_status_t progress_sp2_query(void* stream, progress_info_t* info);

@@ -324,28 +324,19 @@ def cheb_plan(k, m, mu, beta, emin, emax):
 
 
 def cheb_choose_km(terms, mu, beta, emin, emax, max_growth=8.0):
-    """Pick (k, m) for cheb_fermi with k m >= terms: the fewest matrix products
-    ((k - 1) + (m - 1)) among the splits whose nested sums stay within max_growth
-    (the plan's growth = sum |d_ij|; a large growth amplifies the products'
-    rounding, e.g. k = m = 32 at beta b = 236 gives 3e5). Ties go to fewer terms.
-    Host only (uses cheb_plan). Raises ValueError if no split qualifies."""
-    import math
-    best = None
-    for k in range(1, 65):
-        m = max(1, math.ceil(terms / k))
-        if m > 64:
-            continue
-        plan = cheb_plan(k, m, mu, beta, emin, emax)
-        growth = float(abs(plan["d"]).sum())
-        if growth > max_growth:
-            continue
-        key = ((k - 1) + (m - 1), k * m)
-        if best is None or key < best[0]:
-            best = (key, k, m, growth)
-    if best is None:
-        raise ValueError("no (k, m) with k m >= terms keeps the growth within max_growth")
-    return {"k": best[1], "m": best[2], "products": best[0][0], "terms": best[0][1],
-            "growth": best[3]}
+    """Pick (k, m) for cheb_fermi with k m >= terms (progress_cheb_choose, host
+    only): the fewest matrix products of the library's own plan among the
+    splits whose nested sums stay within max_growth (the plan's growth =
+    sum |d_ij|; a large growth amplifies the products' rounding, e.g. k = m =
+    32 at beta b = 236 gives 3e5). Ties go to fewer terms. Raises ProgressError
+    (EINVAL) if no split qualifies."""
+    k, m, p = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    g = ctypes.c_double(0.0)
+    check(load().progress_cheb_choose(int(terms), float(mu), float(beta), float(emin),
+                                      float(emax), float(max_growth), ctypes.byref(k),
+                                      ctypes.byref(m), ctypes.byref(p), ctypes.byref(g)))
+    return {"k": k.value, "m": m.value, "products": p.value, "terms": k.value * m.value,
+            "growth": g.value}
 
 
 def query(stream=None):

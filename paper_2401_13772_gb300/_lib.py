@@ -116,6 +116,8 @@ SIGNATURES = {
                                            ctypes.c_int32, _P, _P, ctypes.POINTER(ChebInfo),
                                            _P]),
     "progress_cheb_slot": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "progress_cheb_choose": (ctypes.c_int, [ctypes.c_int32, _D, _D, _D, _D, _D, _P, _P, _P,
+                                            _P]),
     "progress_cheb_plan": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _D, _D, _D, _D,
                                           ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
     "progress_features": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P]),
@@ -126,7 +128,7 @@ SIGNATURES = {
     "progress_learned_labels": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _D, _P, _P,
                                                _P, _P]),
     "progress_learned_margin": (ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_int32, _P,
-                                               ctypes.c_int32, _D, _D, _P, _P]),
+                                               ctypes.c_int32, _D, _D, _P]),
     "progress_trace_hd": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
     "progress_mlp_param_count": (ctypes.c_int32, [ctypes.c_int32] * 3),
     "progress_mlp_scratch_floats": (ctypes.c_int64, [ctypes.c_int32] * 4),

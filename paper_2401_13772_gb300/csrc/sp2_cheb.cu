@@ -957,6 +957,45 @@ extern "C" progress_status_t progress_cheb_plan(int32_t k, int32_t m, double mu,
   return PROGRESS_OK;
 }
 
+extern "C" progress_status_t progress_cheb_choose(int32_t terms, double mu, double beta,
+                                                  double emin, double emax, double max_growth,
+                                                  int32_t* k_out, int32_t* m_out,
+                                                  int32_t* products_out, double* growth_out) {
+  using namespace sp2;
+  if (terms < 1 || terms > MAX_K * MAX_M) return cfail(PROGRESS_EINVAL, "terms must be in [1, 4096]");
+  if (!isfinite(mu) || !isfinite(beta) || beta < 0.0)
+    return cfail(PROGRESS_EINVAL, "mu must be finite and beta finite and >= 0");
+  if (!(max_growth > 0.0)) return cfail(PROGRESS_EINVAL, "max_growth must be > 0");
+  if (!k_out || !m_out) return cfail(PROGRESS_EINVAL, "NULL output pointer");
+  // every split k m >= terms (m = ceil(terms / k)); the plan that progress_cheb_fermi
+  // would run, ranked by its product count, then by its term count
+  int best_k = 0, best_m = 0, best_p = 0, best_terms = 0;
+  double best_g = 0.0;
+  for (int k = 1; k <= MAX_K; ++k) {
+    const int m = (terms + k - 1) / k;
+    if (m > MAX_M) continue;
+    Plan plan;
+    if (!make_plan(k, m, mu, beta, emin, emax, &plan))
+      return cfail(PROGRESS_EINVAL, "spectral bounds must be finite with emin <= emax");
+    if (!(plan.growth <= max_growth)) continue;
+    const int np = (int)plan.prods.size();
+    if (best_k == 0 || np < best_p || (np == best_p && k * m < best_terms)) {
+      best_k = k;
+      best_m = m;
+      best_p = np;
+      best_terms = k * m;
+      best_g = plan.growth;
+    }
+  }
+  if (best_k == 0)
+    return cfail(PROGRESS_EINVAL, "no (k, m) with k m >= terms keeps the growth within max_growth");
+  *k_out = best_k;
+  *m_out = best_m;
+  if (products_out) *products_out = best_p;
+  if (growth_out) *growth_out = best_g;
+  return PROGRESS_OK;
+}
+
 extern "C" progress_status_t progress_cheb_slot(int32_t slot, int32_t slice, uint16_t* host_out,
                                                 void* stream) {
   using namespace sp2;

@@ -184,9 +184,9 @@ progress_status_t progress_learned_labels(int32_t batch, const int32_t* h_n,
   return st;
 }
 
-progress_status_t progress_learned_margin(int32_t batch, const float* d_y, int32_t ld_y,
-                                          const float* d_t, int32_t ld_t, double quantile,
-                                          double floor, double* margin_out, void* stream) {
+progress_status_t progress_learned_margin(int32_t batch, const float* h_y, int32_t ld_y,
+                                          const float* h_t, int32_t ld_t, double quantile,
+                                          double floor, double* margin_out) {
   if (batch < 0 || ld_y < 2 || ld_t < 2) return lfail(PROGRESS_EINVAL, "bad sizes");
   if (!(quantile >= 0.0 && quantile <= 1.0)) return lfail(PROGRESS_EINVAL, "quantile in [0, 1]");
   if (!margin_out) return lfail(PROGRESS_EINVAL, "NULL margin_out");
@@ -194,23 +194,17 @@ progress_status_t progress_learned_margin(int32_t batch, const float* d_y, int32
     *margin_out = floor;
     return PROGRESS_OK;
   }
-  if (!d_y || !d_t) return lfail(PROGRESS_EINVAL, "NULL pointer argument");
-  std::vector<float> y((size_t)2 * batch), t((size_t)2 * batch);
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpy2DAsync(y.data(), 2 * sizeof(float), d_y, (size_t)ld_y * sizeof(float),
-                                    2 * sizeof(float), batch, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(t.data(), 2 * sizeof(float), d_t, (size_t)ld_t * sizeof(float),
-                          2 * sizeof(float), batch, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return lcuda(e, "learned margin readback");
+  if (!h_y || !h_t) return lfail(PROGRESS_EINVAL, "NULL pointer argument");
   // overshoot of the predicted bound fractions over their targets, the larger
   // of the two per instance; its `quantile` (linear interpolation between
   // order statistics), never below `floor`
   std::vector<double> over((size_t)batch);
-  for (int i = 0; i < batch; ++i)
-    over[i] = std::max(std::max((double)y[2 * i] - (double)t[2 * i], 0.0),
-                       std::max((double)y[2 * i + 1] - (double)t[2 * i + 1], 0.0));
+  for (int i = 0; i < batch; ++i) {
+    const float* y = h_y + (size_t)i * ld_y;
+    const float* t = h_t + (size_t)i * ld_t;
+    over[i] = std::max(std::max((double)y[0] - (double)t[0], 0.0),
+                       std::max((double)y[1] - (double)t[1], 0.0));
+  }
   std::sort(over.begin(), over.end());
   const double pos = quantile * (double)(batch - 1);
   const int lo = (int)pos;

@@ -13,9 +13,11 @@ the SP2 loop. Labels come from SP2 runs of the library itself:
   safety margin the predictions will be widened by.
 
 Training and inference run the library's own kernels (forward, loss,
-backward, Adam; FP16 weights at inference). At solve time the trace-driven
-rule judges every predicted branch; a disagreement beyond the judge margin,
-or a run that leaves [0, 1], sends that instance back to the plain path
+backward, Adam; FP16 weights at inference); the labels, training targets,
+predicted bounds, branch bits and their confident prefix come from the
+library's progress_learned_* calls. At solve time the trace-driven rule
+judges every predicted branch; a disagreement beyond the judge margin, or a
+run that leaves [0, 1], sends that instance back to the plain path
 (Gershgorin bounds, trace rule). This module only marshals torch tensors.
 """
 
@@ -101,40 +103,79 @@ def batched_solve(batch, nocc, tol=1e-10, bounds=None, pred_bits=None, pred_len=
             "fallback": fb, "products": prod}
 
 
-def extremal_eigenvalues(batch, tol=1e-10):
-    """(eps_1, eps_N, emin_G, emax_G) per instance from SP2 runs of the library.
-
-    eps_1 = Tr(H D) with D the SP2 projector of H for nocc = 1 (its lowest
-    state); eps_N the same for -H, negated. A Rayleigh quotient of a projector
-    is second-order accurate in the projector's error."""
-    n = np.asarray(batch["n"])
-    r1 = batched_solve(batch, np.ones_like(n), tol)
-    e1 = trace_hd(batch, r1["D"])
-    neg = dict(batch)
-    neg["H"] = -batch["H"]
-    rN = batched_solve(neg, np.ones_like(n), tol)
-    eN = trace_hd(batch, rN["D"])
-    return e1, eN, r1["bounds"][:, 0].clone(), r1["bounds"][:, 1].clone()
-
-
-def bits_tensor_to_array(bits, length):
-    """[B,4] int64 (uint64 words) -> [B, length] float32 0/1."""
+def labels(batch, tol=1e-10):
+    """Bound labels from SP2 runs of the library (progress_learned_labels):
+    u [B, 2] float32 bound fractions (u_min, u_max of the Gershgorin width),
+    gersh [B, 2] float64 Gershgorin enclosure, eps [2, B] float64 (eps_1, eps_N)."""
     import torch
-    w = bits.to(torch.int64)
-    out = torch.zeros((bits.shape[0], length), dtype=torch.float32, device=bits.device)
-    for k in range(length):
-        out[:, k] = ((w[:, k // 64] >> (k % 64)) & 1).to(torch.float32)
-    return out
+    dev = batch["H"].device
+    B = len(batch["n"])
+    u = torch.empty((B, 2), dtype=torch.float32, device=dev)
+    gersh = torch.empty((B, 2), dtype=torch.float64, device=dev)
+    eps = torch.empty((2, B), dtype=torch.float64, device=dev)
+    n = np.ascontiguousarray(batch["n"], dtype=np.int32)
+    off = np.ascontiguousarray(batch["offsets"], dtype=np.int64)
+    check(load().progress_learned_labels(
+        B, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(off.ctypes.data), _p(batch["d_n"]),
+        _p(batch["d_off"]), _p(batch["H"]), float(tol), _p(u), _p(gersh), _p(eps),
+        _stream_ptr()))
+    return {"u": u, "gersh": gersh, "eps": eps}
 
 
-def array_to_bits_tensor(arr):
-    """[B, L] 0/1 -> [B,4] int64 words."""
+def targets(ub, kmax, bits=None, iters=None, reject=None):
+    """Training targets and masks [B, 2 + kmax] (progress_learned_targets): the
+    bound targets from the first two columns of ub ([B, >= 2] float32), then
+    the branch bits of a labelled run (bits [B, 4] words), masked beyond its
+    product count (iters) and for rejected runs (reject != 0)."""
     import torch
-    B, L = arr.shape
-    words = torch.zeros((B, 4), dtype=torch.int64, device=arr.device)
-    for k in range(min(L, 256)):
-        words[:, k // 64] |= (arr[:, k] > 0.5).to(torch.int64) << (k % 64)
-    return words
+    B, ld = ub.shape
+    T = torch.empty((B, N_BOUNDS + kmax), dtype=torch.float32, device=ub.device)
+    M = torch.empty_like(T)
+    check(load().progress_learned_targets(
+        B, int(kmax), _p(ub), ld, None if bits is None else _p(bits),
+        None if iters is None else _p(iters), None if reject is None else _p(reject), _p(T),
+        _p(M), _stream_ptr()))
+    return T, M
+
+
+def solve_inputs(Y, gersh, margin, logit_tau=None):
+    """Solve inputs from the predictor's outputs Y [B, 2 + kmax]
+    (progress_learned_inputs): bounds [B, 2], the predicted fractions widened by
+    margin and kept inside the Gershgorin enclosure gersh [B, 2]; with
+    logit_tau, also the branch bits [B, 4] (1 iff logit > 0) and the length of
+    the confident prefix [B] (leading logits with |logit| >= logit_tau)."""
+    import torch
+    B, nout = Y.shape
+    bounds = torch.empty((B, 2), dtype=torch.float64, device=Y.device)
+    bits = plen = None
+    if logit_tau is not None:
+        bits = torch.empty((B, 4), dtype=torch.int64, device=Y.device)
+        plen = torch.empty(B, dtype=torch.int32, device=Y.device)
+    check(load().progress_learned_inputs(
+        B, nout, _p(Y), _p(gersh), float(margin),
+        float(logit_tau) if logit_tau is not None else 0.0, _p(bounds),
+        None if bits is None else _p(bits), None if plen is None else _p(plen),
+        _stream_ptr()))
+    return bounds, bits, plen
+
+
+def predicted_bounds(Y, gersh, margin):
+    """[B, 2] bounds from predicted fractions, each widened by margin * w and
+    never outside the Gershgorin enclosure gersh [B, 2]."""
+    return solve_inputs(Y, gersh, margin)[0]
+
+
+def calibrate_margin(Y, T, quantile=0.97, floor=0.02):
+    """Margin (fraction of the Gershgorin width) that covers the predicted
+    bounds' overshoot on held-out instances (progress_learned_margin, on the
+    bound columns copied to the host)."""
+    y = np.ascontiguousarray(Y[:, :2].cpu().numpy(), dtype=np.float32)
+    t = np.ascontiguousarray(T[:, :2].cpu().numpy(), dtype=np.float32)
+    out = ctypes.c_double(0.0)
+    check(load().progress_learned_margin(y.shape[0], ctypes.c_void_p(y.ctypes.data), 2,
+                                         ctypes.c_void_p(t.ctypes.data), 2, float(quantile),
+                                         float(floor), ctypes.byref(out)))
+    return out.value
 
 
 class Predictor:
@@ -218,70 +259,14 @@ class Predictor:
         return Y
 
 
-def bound_fractions(eps1, epsN, emin, emax):
-    """u_min = (eps_1 - emin)/w, u_max = (emax - eps_N)/w with w = emax - emin."""
-    import torch
-    w = emax - emin
-    return (torch.clamp((eps1 - emin) / w, min=0.0), torch.clamp((emax - epsN) / w, min=0.0))
-
-
-def predicted_bounds(Y, emin, emax, margin):
-    """[B, 2] bounds from predicted fractions, each widened by margin * w and
-    never outside the Gershgorin enclosure."""
-    import torch
-    w = emax - emin
-    u0 = torch.clamp(Y[:, 0].double() - margin, min=0.0)
-    u1 = torch.clamp(Y[:, 1].double() - margin, min=0.0)
-    lo = emin + w * u0
-    hi = emax - w * u1
-    ok = hi > lo
-    lo = torch.where(ok, lo, emin)
-    hi = torch.where(ok, hi, emax)
-    return torch.stack([lo, hi], dim=1).contiguous()
-
-
-def calibrate_margin(Y, T, quantile=0.97, floor=0.02):
-    """Margin (fraction of the Gershgorin width) that covers the predicted
-    bounds' overshoot on held-out instances: the `quantile` of
-    max(y_j - t_j) over both bounds, never below `floor`. A run whose bounds
-    cut the spectrum is rejected by the judge and restarts on the plain path,
-    so the quantile sets the expected fallback rate of that cause."""
-    import torch
-    over = torch.clamp(Y[:, :2].double() - T[:, :2].double(), min=0.0).max(dim=1).values
-    if over.numel() == 0:
-        return float(floor)
-    return max(float(floor), float(torch.quantile(over, quantile).item()))
-
-
-def make_targets(u_min, u_max, bits, iters, kmax):
-    """Targets and masks: the two bound fractions, then the branch bits of the
-    labelled SP2 run (masked beyond its product count)."""
-    import torch
-    B = u_min.shape[0]
-    dev = u_min.device
-    T = torch.zeros((B, N_BOUNDS + kmax), dtype=torch.float32, device=dev)
-    M = torch.zeros_like(T)
-    T[:, 0] = u_min.float()
-    T[:, 1] = u_max.float()
-    M[:, :N_BOUNDS] = 1.0
-    T[:, N_BOUNDS:] = bits_tensor_to_array(bits, kmax)
-    ks = torch.arange(kmax, device=dev)
-    M[:, N_BOUNDS:] = (ks[None, :] < iters[:, None].to(torch.int64)).float()
-    return T, M
-
-
 def label_batch(batch, nocc, margin, kmax, tol=1e-10):
     """Features and bound targets of one packed batch (SP2-derived labels);
     the branch targets are filled by ``branch_labels`` once bounds can be
     predicted."""
     feat = features(batch)
-    e1, eN, emin, emax = extremal_eigenvalues(batch, tol)
-    u_min, u_max = bound_fractions(e1, eN, emin, emax)
-    import torch
-    iters0 = torch.zeros_like(u_min, dtype=torch.int32)
-    bits0 = torch.zeros((u_min.shape[0], 4), dtype=torch.int64, device=u_min.device)
-    T, M = make_targets(u_min, u_max, bits0, iters0, kmax)
-    return {"X": feat, "T": T, "M": M, "emin": emin, "emax": emax, "eps1": e1, "epsN": eN}
+    lab = labels(batch, tol)
+    T, M = targets(lab["u"], kmax)
+    return {"X": feat, "T": T, "M": M, "gersh": lab["gersh"], "eps": lab["eps"]}
 
 
 def branch_labels(pred, batch, nocc, lab, margin, tol=1e-10):
@@ -290,35 +275,16 @@ def branch_labels(pred, batch, nocc, lab, margin, tol=1e-10):
     targets replaced by ``pred``'s own outputs so that further training keeps
     those bounds while it learns the branches."""
     Y = pred.predict(lab["X"])
-    bounds = predicted_bounds(Y, lab["emin"], lab["emax"], margin)
-    run = batched_solve(batch, nocc, tol, bounds=bounds)
-    ok = run["fallback"] == 0
+    run = batched_solve(batch, nocc, tol, bounds=predicted_bounds(Y, lab["gersh"], margin))
     kmax = lab["T"].shape[1] - N_BOUNDS
-    T, M = make_targets(Y[:, 0].double(), Y[:, 1].double(), run["bits"], run["iters"], kmax)
-    M[~ok, N_BOUNDS:] = 0.0  # a run that failed gives no branch labels
-    return T, M
+    return targets(Y, kmax, bits=run["bits"], iters=run["iters"], reject=run["fallback"])
 
 
-def confident_prefix(logits, tau):
-    """Per row, the number of leading branch logits with |logit| >= tau: only
-    that prefix of the sequence is predicted; later branches are left to the
-    trace rule (no prediction to judge)."""
-    import torch
-    conf = (logits.abs() >= tau).to(torch.int32)
-    # length of the leading run of ones
-    run = torch.cumprod(conf, dim=1)
-    return run.sum(dim=1).to(torch.int32).contiguous()
-
-
-def solve_learned(pred, batch, nocc, emin, emax, margin, judge_delta, tau=2.0, tol=1e-10):
+def solve_learned(pred, batch, nocc, gersh, margin, judge_delta, tau=2.0, tol=1e-10):
     """Batched solve with predicted bounds and the confident prefix of the
     predicted branch sequence, judged by the trace rule."""
-    X = features(batch)
-    Y = pred.predict(X)
-    bounds = predicted_bounds(Y, emin, emax, margin)
-    logits = Y[:, N_BOUNDS:]
-    bits = array_to_bits_tensor((logits > 0).float())
-    plen = confident_prefix(logits, tau)
+    Y = pred.predict(features(batch))
+    bounds, bits, plen = solve_inputs(Y, gersh, margin, logit_tau=tau)
     out = batched_solve(batch, nocc, tol, bounds=bounds, pred_bits=bits, pred_len=plen,
                         judge_delta=judge_delta)
     out["pred_len"] = plen

@@ -130,12 +130,16 @@ def test_chooser_prefers_stable_splits(pkg):
     assert float(np.abs(sharp["d"]).sum()) > 1e4
     r = pkg.cheb_choose_km(1024, 0.5, 4.0, emin, emax)
     assert r["k"] * r["m"] >= 1024 and r["growth"] <= 8.0 and r["k"] > r["m"]
-    # every split with fewer products exceeds the growth bound
+    # every split whose plan has fewer products exceeds the growth bound
     for k in range(1, 65):
         m = -(-1024 // k)
-        if m <= 64 and (k - 1) + (m - 1) < r["products"]:
-            assert float(np.abs(pkg.cheb_plan(k, m, 0.5, 4.0, emin, emax)["d"]).sum()) > 8.0
-    with pytest.raises(ValueError):
+        if m > 64:
+            continue
+        plan = pkg.cheb_plan(k, m, 0.5, 4.0, emin, emax)
+        if len(plan["prods"]) < r["products"]:
+            assert float(np.abs(plan["d"]).sum()) > 8.0
+    assert len(pkg.cheb_plan(r["k"], r["m"], 0.5, 4.0, emin, emax)["prods"]) == r["products"]
+    with pytest.raises(pkg.ProgressError):
         pkg.cheb_choose_km(1024, 0.5, 4.0, emin, emax, max_growth=1e-3)
 
 

@@ -35,22 +35,72 @@ def test_features_match_oracle(L):
         assert abs(row[36] - ref[36]) <= 1e-7
 
 
-def test_trace_hd_and_extremal_eigenvalues(L):
+def test_trace_hd_and_labels(L):
     import torch
     mats = [cube_hamiltonian(s, 7 + s)[0] for s in (20, 48, 96)]
     b = L.to_device_batch(mats)
     D = torch.from_numpy(np.concatenate([np.eye(m.shape[0]).ravel() for m in mats])).cuda()
     t = L.trace_hd(b, D).cpu().numpy()
     assert np.allclose(t, [np.trace(m) for m in mats], atol=1e-4)
-    e1, eN, lo, hi = L.extremal_eigenvalues(b)
-    for H, a, z, g0, g1 in zip(mats, e1.cpu().numpy(), eN.cpu().numpy(), lo.cpu().numpy(),
-                               hi.cpu().numpy()):
+    lab = L.labels(b)
+    eps = lab["eps"].cpu().numpy()
+    gersh = lab["gersh"].cpu().numpy()
+    u = lab["u"].cpu().numpy()
+    for i, H in enumerate(mats):
         w = np.linalg.eigvalsh(H)
         emin, emax = oracle.gershgorin_bounds(H)
-        assert abs(g0 - emin) < 1e-9 and abs(g1 - emax) < 1e-9
+        assert abs(gersh[i, 0] - emin) < 1e-9 and abs(gersh[i, 1] - emax) < 1e-9
         # within the edge degeneracy: between the two lowest (highest) eigenvalues
-        assert w[0] - 1e-3 <= a <= w[1] + 1e-3
-        assert w[-2] - 1e-3 <= z <= w[-1] + 1e-3
+        assert w[0] - 1e-3 <= eps[0, i] <= w[1] + 1e-3
+        assert w[-2] - 1e-3 <= eps[1, i] <= w[-1] + 1e-3
+        # bound fractions of the Gershgorin width, as the definition states them
+        wd = emax - emin
+        assert u[i, 0] == np.float32(max((eps[0, i] - gersh[i, 0]) / (gersh[i, 1] - gersh[i, 0]),
+                                         0.0))
+        assert u[i, 1] == np.float32(max((gersh[i, 1] - eps[1, i]) / (gersh[i, 1] - gersh[i, 0]),
+                                         0.0))
+        assert 0.0 <= u[i, 0] <= (w[1] - emin) / wd + 1e-3
+
+
+def test_solve_inputs_and_targets_follow_their_definitions(L):
+    import torch
+    rng = np.random.default_rng(5)
+    B, kmax, margin, tau = 7, 70, 0.03, 2.0
+    Y = rng.standard_normal((B, 2 + kmax)).astype(np.float32) * 3.0
+    Y[:, :2] = rng.uniform(-0.05, 0.6, (B, 2)).astype(np.float32)
+    Y[3, :2] = [0.7, 0.6]  # crossing predictions -> the Gershgorin enclosure
+    G = np.stack([rng.uniform(-60, -10, B), rng.uniform(5, 60, B)], 1)
+    bounds, bits, plen = L.solve_inputs(torch.from_numpy(Y).cuda(), torch.from_numpy(G).cuda(),
+                                        margin, logit_tau=tau)
+    bounds, bits, plen = bounds.cpu().numpy(), bits.cpu().numpy(), plen.cpu().numpy()
+    for i in range(B):
+        w = G[i, 1] - G[i, 0]
+        lo = G[i, 0] + w * max(float(Y[i, 0]) - margin, 0.0)
+        hi = G[i, 1] - w * max(float(Y[i, 1]) - margin, 0.0)
+        if not hi > lo:
+            lo, hi = G[i, 0], G[i, 1]
+        assert bounds[i, 0] == lo and bounds[i, 1] == hi
+        word = [0, 0, 0, 0]
+        for k in range(kmax):
+            if Y[i, 2 + k] > 0:
+                word[k // 64] |= 1 << (k % 64)
+        assert [int(v) & (2 ** 64 - 1) for v in bits[i]] == word
+        L_ = 0
+        while L_ < kmax and abs(Y[i, 2 + L_]) >= tau:
+            L_ += 1
+        assert plen[i] == L_
+    assert bounds[3, 0] == G[3, 0] and bounds[3, 1] == G[3, 1]
+    # targets and masks
+    iters = torch.tensor([0, 5, 70, 80, 3, 64, 65], dtype=torch.int32, device="cuda:0")
+    reject = torch.tensor([0, 0, 0, 0, 1, 0, 0], dtype=torch.int32, device="cuda:0")
+    wb = torch.from_numpy(rng.integers(-2 ** 62, 2 ** 62, (B, 4))).cuda()
+    T, M = L.targets(torch.from_numpy(Y).cuda(), kmax, bits=wb, iters=iters, reject=reject)
+    T, M, wbh = T.cpu().numpy(), M.cpu().numpy(), wb.cpu().numpy()
+    for i in range(B):
+        assert T[i, 0] == Y[i, 0] and T[i, 1] == Y[i, 1] and M[i, 0] == 1 and M[i, 1] == 1
+        for k in range(kmax):
+            assert T[i, 2 + k] == float((int(wbh[i, k // 64]) >> (k % 64)) & 1)
+            assert M[i, 2 + k] == float(k < int(iters[i]) and not int(reject[i]))
 
 
 def _rand_problem(seed, B=40, kmax=12, hidden=32):
@@ -111,8 +161,9 @@ def test_judge_rejects_wrong_predictions_and_keeps_d(L):
     assert r["fallback"].cpu().numpy().tolist() == [1] * B
     assert (r["D"] - plain["D"]).abs().max().item() <= 1e-6
     # the real sequence and exact-ish bounds are accepted
-    e1, eN, g0, g1 = L.extremal_eigenvalues(b)
-    w = g1 - g0
+    lab = L.labels(b)
+    e1, eN = lab["eps"][0], lab["eps"][1]
+    w = lab["gersh"][:, 1] - lab["gersh"][:, 0]
     good = torch.stack([e1 - 0.02 * w, eN + 0.02 * w], 1).contiguous()
     r = L.batched_solve(b, nocc, bounds=good)
     assert r["fallback"].sum().item() == 0
@@ -141,10 +192,10 @@ def test_trained_predictor_saves_iterations(L):
     ev = L.to_device_batch(mats)
     nocc = [m.shape[0] // 2 for m in mats]
     plain = L.batched_solve(ev, nocc)
-    g0, g1 = plain["bounds"][:, 0], plain["bounds"][:, 1]
+    gersh = plain["bounds"]
     Y = P.predict(L.features(ev))
-    rb = L.batched_solve(ev, nocc, bounds=L.predicted_bounds(Y, g0, g1, margin))
-    lr = L.solve_learned(P, ev, nocc, g0, g1, margin, judge_delta=0.5)
+    rb = L.batched_solve(ev, nocc, bounds=L.predicted_bounds(Y, gersh, margin))
+    lr = L.solve_learned(P, ev, nocc, gersh, margin, judge_delta=0.5)
     pp = plain["products"].double().mean().item()
     pb = rb["products"].double().mean().item()
     pl = lr["products"].double().mean().item()
