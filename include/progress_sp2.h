@@ -120,9 +120,13 @@ typedef struct {
 typedef struct {
   int32_t status;        /* progress_status_t of the solve */
   int32_t iters;         /* products performed */
-  int32_t converged;     /* 1 if |Tr X^2 - Tr X| < tol was reached, or (MIXED modes) the
-                            refinement stopped on the round-off floor of its products
-                            (two steps without halving the error) */
+  int32_t converged;     /* 1 if |Tr X^2 - Tr X| < tol was reached; 2 (MIXED modes) if the
+                            refinement stopped on the round-off floor of its FP64-accurate
+                            products before reaching tol: |Tr X^2 - Tr X| < 2 n u and
+                            |Tr X - nocc| < n u / 2 (u = 2^-40 for digit products, 2^-44
+                            double-float, 2^-52 native FP64), or two refinement products
+                            that did not halve |Tr X^2 - Tr X|. The reached
+                            value is in `idempotency`; the status is still PROGRESS_OK */
   int32_t phase_iters[3];/* products in FP64 prefix / split phase / FP64 refinement */
   double emin, emax;     /* bounds used */
   double trace;          /* Tr D */
@@ -139,13 +143,13 @@ void progress_opts_default(progress_opts_t* opts);
 /*
  * Gershgorin enclosure of the spectrum of the symmetric H (§VIII.A; the emin,
  * emax that Listing 1 uses): R_i = sum_{j != i} |H_ij|,
- * d_bounds[0] = min_i (H_ii - R_i), d_bounds[1] = max_i (H_ii + R_i).
- *   dH        device, n x n FP64 row-major, read only
- *   d_bounds  device, 2 doubles, written
- * Errors: EINVAL if n < 1 or a pointer is NULL.
+ * *d_emin = min_i (H_ii - R_i), *d_emax = max_i (H_ii + R_i).
+ *   dH              device, n x n FP64 row-major, read only
+ *   d_emin, d_emax  device, one double each, written
+ * Asynchronous. Errors: EINVAL if n < 1 or a pointer is NULL.
  */
-progress_status_t progress_gershgorin_bounds(const double* dH, int64_t n, double* d_bounds,
-                                             void* stream);
+progress_status_t progress_gershgorin_bounds(const double* dH, int64_t n, double* d_emin,
+                                             double* d_emax, void* stream);
 
 /*
  * SP2 density matrix with default options (FP64 products, nearer rule,
@@ -176,11 +180,11 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
 /*
  * FP64 SP2 solve (same arithmetic and defaults as progress_sp2_dense) that
  * allocates no memory at all. The paper has no counterpart: this entry point
- * exists for callers that cannot call cudaMalloc -- code running while a
- * stream is captured in global capture mode, where cudaMalloc is a
- * prohibited call; applications whose memory pool already owns the whole
- * device; and time-stepping codes (QMD calls the solver every step) that
- * must not pay allocation latency. The caller still passes H and D.
+ * exists for callers that cannot call cudaMalloc -- applications whose own
+ * memory pool already owns the whole device, so an allocation by the library
+ * would fail or fragment it, and time-stepping codes (QMD calls the solver
+ * every step) that must not pay allocation latency or the device-wide
+ * synchronization of cudaFree. The caller still passes H and D.
  *   Limit: n <= 1024; larger n returns PROGRESS_EINVAL.
  *   Work space: one static device array of about 16.1 MiB inside the library
  *   (every GPU that loads the library holds it until the process exits). Its

@@ -59,6 +59,7 @@ def gershgorin_bounds(H, out=None, stream=None):
     with torch.cuda.device(H.device):
         check(load().progress_gershgorin_bounds(ctypes.c_void_p(H.data_ptr()), H.shape[0],
                                                 ctypes.c_void_p(out.data_ptr()),
+                                                ctypes.c_void_p(out.data_ptr() + 8),
                                                 _stream_ptr(stream)))
     return out
 

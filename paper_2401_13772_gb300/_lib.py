@@ -42,6 +42,7 @@ class Info(ctypes.Structure):
         bits = [(self.bits[k // 64] >> (k % 64)) & 1 for k in range(self.iters)]
         return {"status": STATUS_NAMES.get(self.status, str(self.status)),
                 "iters": self.iters, "converged": bool(self.converged),
+                "floor_stop": self.converged == 2,
                 "phase_iters": list(self.phase_iters), "emin": self.emin,
                 "emax": self.emax, "trace": self.trace,
                 "idempotency": self.idempotency, "bits": bits, "kblocks": self.kblocks}
@@ -88,7 +89,7 @@ class BatchTune(ctypes.Structure):
     def to_dict(self):
         return {"tile_n": self.tile_n, "cluster": self.cluster, "share": self.share,
                 "candidates": [{"tile_n": self.cand[i][0], "cluster": self.cand[i][1],
-                                "share": self.cand[i][2], "ms": round(float(self.ms[i]), 3)}
+                                "share": self.cand[i][2], "ms": float(self.ms[i])}
                                for i in range(self.ncand)]}
 
 
@@ -98,7 +99,7 @@ _I64 = ctypes.c_int64
 _D = ctypes.c_double
 SIGNATURES = {
     "progress_opts_default": (None, [ctypes.POINTER(Opts)]),
-    "progress_gershgorin_bounds": (ctypes.c_int, [_P, _I64, _P, _P]),
+    "progress_gershgorin_bounds": (ctypes.c_int, [_P, _I64, _P, _P, _P]),
     "progress_sp2_dense": (ctypes.c_int, [_P, _I64, _I64, _D, _P, _P]),
     "progress_sp2_dense_ex": (ctypes.c_int, [_P, _I64, _I64, _D, _P, ctypes.POINTER(Opts),
                                              ctypes.POINTER(Info), _P]),

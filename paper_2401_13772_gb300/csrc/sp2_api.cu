@@ -323,9 +323,10 @@ const char* progress_last_error(void) { return g_err.c_str(); }
 
 const char* progress_version(void) { return "0.1.0"; }
 
-progress_status_t progress_gershgorin_bounds(const double* dH, int64_t n, double* d_bounds,
-                                             void* stream) {
-  if (n < 1 || !dH || !d_bounds) return fail(PROGRESS_EINVAL, "gershgorin: n < 1 or NULL pointer");
+progress_status_t progress_gershgorin_bounds(const double* dH, int64_t n, double* d_emin,
+                                             double* d_emax, void* stream) {
+  if (n < 1 || !dH || !d_emin || !d_emax)
+    return fail(PROGRESS_EINVAL, "gershgorin: n < 1 or NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
   Workspace* w = nullptr;
   progress_status_t st = get_workspace(s, &w);
@@ -341,7 +342,7 @@ progress_status_t progress_gershgorin_bounds(const double* dH, int64_t n, double
   p.emin_override = NAN;
   p.emax_override = NAN;
   CK(sp2::launch_init(w->buf, p, s), "init launch");
-  CK(sp2::launch_gershgorin(dH, n, w->buf, d_bounds, s), "gershgorin launch");
+  CK(sp2::launch_gershgorin(dH, n, w->buf, d_emin, d_emax, s), "gershgorin launch");
   return PROGRESS_OK;
 }
 
@@ -440,9 +441,14 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   p.wait_ns = o.wait_limit_us > 0 ? 1000ull * (unsigned long long)o.wait_limit_us
                                   : 2000000000ull;
   p.stall_test = o.stall_test;
+  // round-off floor of the refinement: 2 n u with u the absolute accuracy of
+  // one FP64-accurate product entry (digit products ~2^-40, double-float
+  // ~2^-44, native FP64 ~2^-52; entries of X are at most 1)
+  p.floor_acc = 2.0 * (double)n * (oz ? 9.094947017729282e-13 : df64 ? 5.684341886080802e-14
+                                                                   : 2.220446049250313e-16);
 
   CK(sp2::launch_init(w->buf, p, s), "init launch");
-  CK(sp2::launch_gershgorin(dH, n, w->buf, nullptr, s), "gershgorin launch");
+  CK(sp2::launch_gershgorin(dH, n, w->buf, nullptr, nullptr, s), "gershgorin launch");
   CK(sp2::launch_x0(dH, w->buf, p, s), "x0 launch");
   if (p.tau > 0.0f) CK(sp2::launch_tile_flags(dH, n, ld, w->buf, s), "tile flag launch");
   if (o.loop_events[0]) CK(cudaEventRecord((cudaEvent_t)o.loop_events[0], s), "event record");

@@ -67,9 +67,13 @@ struct BCfg {
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = NS * (A_BYTES + B_BYTES);
   static constexpr int STAGES = fmt_bf16(F) ? 2 : (BN == 128 ? 3 : 4);
-  // FP16x2: acc0 (hi*hi) and acc1 (hi*lo + lo*hi, weight 2^-11) per buffer;
-  // BF16x3: the slices carry their own magnitudes, one accumulator.
-  static constexpr int ACC_COLS = NS == 2 ? 2 * BN : BN;
+  // Two accumulators per buffer: acc0 = hi*hi and acc1 = the correction
+  // products (FP16x2: hi*lo + lo*hi, weight 2^-11; BF16x3: hi*mid + mid*hi +
+  // hi*lo + lo*hi + mid*mid, weight 1). The tensor core's FP32 accumulation
+  // truncates; adding the small correction terms into the leading sum would
+  // drop their low bits every time (a systematic bias), so they are summed on
+  // their own scale.
+  static constexpr int ACC_COLS = 2 * BN;
   static constexpr int TMEM_COLS = 2 * ACC_COLS;
   static constexpr int COLS_PER_WARP = BN / 2;
   // epilogue staging per warp: 32 rows x 16 columns of packed (slice0,
@@ -486,13 +490,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                   mma_f16(acc1, a[0] + adv, b[1] + adv, idesc, acc);
                   mma_f16(acc1, a[1] + adv, b[0] + adv, idesc, 1u);
                 } else {
-                  // small terms first, the leading product last
-                  mma_f16(acc0, a[0] + adv, b[2 % NS] + adv, idesc, acc);
-                  mma_f16(acc0, a[2 % NS] + adv, b[0] + adv, idesc, 1u);
-                  mma_f16(acc0, a[1] + adv, b[1] + adv, idesc, 1u);
-                  mma_f16(acc0, a[0] + adv, b[1] + adv, idesc, 1u);
-                  mma_f16(acc0, a[1] + adv, b[0] + adv, idesc, 1u);
-                  mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, 1u);
+                  // the corrections, small terms first, then the leading product
+                  mma_f16(acc1, a[0] + adv, b[2 % NS] + adv, idesc, acc);
+                  mma_f16(acc1, a[2 % NS] + adv, b[0] + adv, idesc, 1u);
+                  mma_f16(acc1, a[1] + adv, b[1] + adv, idesc, 1u);
+                  mma_f16(acc1, a[0] + adv, b[1] + adv, idesc, 1u);
+                  mma_f16(acc1, a[1] + adv, b[0] + adv, idesc, 1u);
+                  mma_f16(acc0, a[0] + adv, b[0] + adv, idesc, acc);
                 }
               }
               mma_commit(empty_bar(s));
@@ -542,14 +546,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 uint32_t u0[16], u1[16];
                 tmem_ld16(tmem + lane_base + ACC_COLS * tb + cofs + hh * 16, u0);
-                if (NS == 2) tmem_ld16(tmem + lane_base + ACC_COLS * tb + BN + cofs + hh * 16, u1);
+                tmem_ld16(tmem + lane_base + ACC_COLS * tb + BN + cofs + hh * 16, u1);
                 tmem_ld_wait();
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {
                   const int c = c0 + hh * 16 + jj;
                   float x = (NS == 2)
                                 ? __uint_as_float(u0[jj]) + __uint_as_float(u1[jj]) * (1.0f / 2048.0f)
-                                : __uint_as_float(u0[jj]);
+                                : __uint_as_float(u0[jj]) + __uint_as_float(u1[jj]);
                   if (bit)
                     x = 2.0f * join_value<F>((uint16_t)(m01[jj] & 0xffffu),
                                              (uint16_t)(m01[jj] >> 16), (uint16_t)m2[jj]) -

@@ -788,7 +788,7 @@ progress_status_t run(const double* dH, int64_t n, double mu, double beta, int k
     emin = h_bounds[0];
     emax = h_bounds[1];
   } else {
-    progress_status_t st = progress_gershgorin_bounds(dH, n, w->scal, s);
+    progress_status_t st = progress_gershgorin_bounds(dH, n, w->scal, w->scal + 1, s);
     if (st != PROGRESS_OK) return st;
     double hb[2];
     e = cudaMemcpyAsync(hb, w->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);

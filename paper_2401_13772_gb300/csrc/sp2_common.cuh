@@ -38,7 +38,8 @@ struct State {
   double idem;        // |t2 - t1|
   int iter;           // products performed (k)
   int done;           // 1: stop the loop
-  int converged;      // 1: idempotency below tol
+  int converged;      // 1: idempotency below tol; 2: stopped on the round-off floor of
+                      // the FP64-accurate refinement products (MIXED modes)
   int status;         // progress_status_t
   int bit;            // branch of the next product (1: 2X - X^2)
   int phase;          // Phase of the next product
@@ -57,6 +58,8 @@ struct State {
   double judge_delta;
   double y_mu;  // PROGRESS_RULE_MU: the chemical potential under the same map as X_k
   unsigned long long kblocks;  // thresholded SP2: 64-wide k-blocks streamed (all products)
+  double floor_acc;            // MIXED: idempotency below which the FP64-accurate
+                               // refinement has reached its products' round-off floor
   unsigned long long wait_ns;  // bound on each pipeline wait of the tensor-core kernels
   int stall_test;              // 1: CTA 0 of a tensor-core product waits on a barrier that
                                // nothing arrives on (test of the bounded waits)
@@ -168,8 +171,13 @@ __device__ inline void decide(State* st) {
       st->split_stall = 0;
     } else if (phase == kPhaseRefine) {
       // Refinement converges quadratically down to the round-off floor of
-      // its FP64-accurate products (about n times their absolute error):
-      // two steps that do not halve the error mean the floor is reached.
+      // its FP64-accurate products, about n times their absolute error u:
+      // once the idempotency error is below 2 n u (floor_acc) and the trace
+      // is within n u / 2 of Nocc, further products only add noise (measured:
+      // the error then wanders up, not down). Two steps that do not halve the
+      // error also mean the floor is reached.
+      if (idem < st->floor_acc && fabs(t1 - (double)st->nocc) < 0.25 * st->floor_acc)
+        refine_floor = true;
       if (idem < st->best_split_idem * 0.5) {
         st->best_split_idem = idem;
         st->split_stall = 0;
@@ -188,7 +196,7 @@ __device__ inline void decide(State* st) {
   // Convergence is tested in FP64-accurate phases and in the all-split mode.
   if (((phase != kPhaseSplit || st->prec == PROGRESS_FP32_SPLIT) && idem < st->tol) ||
       refine_floor) {
-    st->converged = 1;
+    st->converged = idem < st->tol ? 1 : 2;
     st->done = 1;
     return;
   }

@@ -36,6 +36,7 @@ __global__ void init_kernel(State* st, SolveParams p) {
     st->emax_override = p.emax_override;
     st->best_split_idem = INFINITY;
     st->wait_ns = p.wait_ns;
+    st->floor_acc = p.floor_acc;
     st->stall_test = p.stall_test;
     st->phase = (p.prec == PROGRESS_FP32_SPLIT) ? kPhaseSplit : kPhaseFP64;
   }
@@ -46,7 +47,8 @@ __global__ void init_kernel(State* st, SolveParams p) {
 __global__ void __launch_bounds__(kEwThreads) gershgorin_kernel(const double* __restrict__ H,
                                                                 int64_t n, State* st,
                                                                 double* __restrict__ blk,
-                                                                double* __restrict__ out) {
+                                                                double* __restrict__ out_min,
+                                                                double* __restrict__ out_max) {
   __shared__ double s_lo[kEwThreads / 32], s_hi[kEwThreads / 32];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -103,9 +105,9 @@ __global__ void __launch_bounds__(kEwThreads) gershgorin_kernel(const double* __
     }
     st->emin = e0;
     st->emax = e1;
-    if (out) {
-      out[0] = lo;
-      out[1] = hi;
+    if (out_min && out_max) {
+      *out_min = lo;
+      *out_max = hi;
     }
     st->ticket = 0u;
   }
@@ -243,12 +245,12 @@ cudaError_t launch_init(const DevBuffers& b, const SolveParams& p, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_gershgorin(const double* H, int64_t n, const DevBuffers& b, double* out,
-                              cudaStream_t s) {
+cudaError_t launch_gershgorin(const double* H, int64_t n, const DevBuffers& b, double* out_min,
+                              double* out_max, cudaStream_t s) {
   int64_t blocks = (n + kEwThreads / 32 - 1) / (kEwThreads / 32);
   if (blocks > kEwMaxBlocks) blocks = kEwMaxBlocks;
   if (blocks > b.max_partials) blocks = b.max_partials;
-  gershgorin_kernel<<<(int)blocks, kEwThreads, 0, s>>>(H, n, b.st, b.partials, out);
+  gershgorin_kernel<<<(int)blocks, kEwThreads, 0, s>>>(H, n, b.st, b.partials, out_min, out_max);
   return cudaGetLastError();
 }
 

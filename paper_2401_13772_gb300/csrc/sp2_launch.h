@@ -37,13 +37,14 @@ struct SolveParams {
   float tau;  // thresholded SP2 cutoff (0 = dense)
   unsigned long long wait_ns;  // bound on each pipeline wait of the tensor-core kernels
   int stall_test;              // test of the bounded waits (see progress_opts_t)
+  double floor_acc;            // MIXED: round-off floor of the refinement's idempotency
 };
 
 cudaError_t launch_init(const DevBuffers& b, const SolveParams& p, cudaStream_t s);
-// Gershgorin bounds into st->emin/emax (unless overridden) and, if out != null,
-// into out[0..1].
-cudaError_t launch_gershgorin(const double* H, int64_t n, const DevBuffers& b, double* out,
-                              cudaStream_t s);
+// Gershgorin bounds into st->emin/emax (unless overridden) and, if out_min and
+// out_max are not null, into *out_min and *out_max.
+cudaError_t launch_gershgorin(const double* H, int64_t n, const DevBuffers& b, double* out_min,
+                              double* out_max, cudaStream_t s);
 cudaError_t launch_x0(const double* H, const DevBuffers& b, const SolveParams& p, cudaStream_t s);
 // One FP64 product step (no-op unless the state says the next product is FP64).
 cudaError_t launch_square_fp64(const DevBuffers& b, int ld, int slice_fmt,

@@ -1,9 +1,9 @@
 // progress_sp2_dense_noalloc: the FP64 SP2 solve without any device memory
-// allocation, for callers that cannot call cudaMalloc -- code that runs while
-// a CUDA stream is being captured in global mode (where cudaMalloc is a
-// prohibited call), applications whose memory pool has already reserved the
-// whole device, and time-stepping codes (quantum molecular dynamics calls the
-// solver every step) that must not see allocation latency or fragmentation.
+// allocation, for callers that cannot call cudaMalloc -- applications whose
+// own memory pool has already reserved the whole device (a cudaMalloc from the
+// library would fail or fragment that pool), and time-stepping codes (quantum
+// molecular dynamics calls the solver every step) that must not see allocation
+// latency or the device-wide synchronization that cudaFree implies.
 //
 // Its work space -- the two FP64 ping-pong iterates, the per-CTA partial
 // traces and the solve state -- lives in one file-scope __device__ array of
@@ -100,7 +100,7 @@ extern "C" progress_status_t progress_sp2_dense_noalloc(const double* dH, int64_
   // Plain launches only (no graph is instantiated): the product kernels exit
   // at once after the device-side stop flag is set.
   if (sp2::launch_init(buf, p, s) != cudaSuccess ||
-      sp2::launch_gershgorin(dH, n, buf, nullptr, s) != cudaSuccess ||
+      sp2::launch_gershgorin(dH, n, buf, nullptr, nullptr, s) != cudaSuccess ||
       sp2::launch_x0(dH, buf, p, s) != cudaSuccess)
     return noalloc_fail(PROGRESS_ECUDA, "kernel launch failed");
   for (int i = 0; i <= p.maxiter; ++i)

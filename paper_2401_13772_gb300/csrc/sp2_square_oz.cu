@@ -24,19 +24,23 @@
 // units: the tensor core's FP32 accumulation is exact for them over the whole
 // K. G2 stays below 2^24 units over 128 consecutive k (x1 x1^T contributes
 // up to 256^2 per k); after every such chunk the drain warps move it into
-// int32 registers (exact). T is accumulated in FP32: its terms are below
-// 2^-27 in size, its rounding error about 2^-40. S = G0 + G1 + 2^-34 g2 + T
-// is then summed in double-float (Knuth's two-sum), X' = S or 2X - S, and X'
-// is written back as double-float planes.
+// int32 registers (exact). T (terms below 2^-27) is accumulated in FP32 over
+// the same 128-k chunks and the chunk sums are added in shared memory with
+// round-to-nearest: the tensor core's FP32 accumulation truncates, and T's
+// diagonal entries carry the always-positive x2 x2 term, so one accumulation
+// over the whole K shaved about 1e-11 off every diagonal entry (a trace bias
+// of -8e-8 at n = 8192); short chains remove that bias. S = G0 + G1 + 2^-34
+// g2 + T is then summed in double-float (Knuth's two-sum), X' = S or 2X - S,
+// and X' is written back as double-float planes.
 //
 // Roles (one CTA per 128 x 128 upper-triangle tile, 384 threads):
 //   warp 0 lane 0 : TMA producer, 5 + 5 digit boxes of 128 x 16 (32 B rows,
-//                   32 B swizzle) per stage, five stages
+//                   32 B swizzle) per stage, four stages
 //   warp 1 lane 0 : MMA issuer (kind::f16 with BF16 operands, M = N = 128,
-//                   K = 16); per stage it issues the G2 products first, so
-//                   that at the end of a chunk the drain can read G2 while
-//                   the tensor core works on G0, G1 and T
-//   warps 4..11   : drain (G2 chunks, 64 columns each) and epilogue
+//                   K = 16); per stage it issues the G2 and T products first,
+//                   so that at the end of a chunk the drain can read them
+//                   while the tensor core works on G0 and G1
+//   warps 4..11   : drain (G2 and T chunks, 64 columns each) and epilogue
 // The digit planes come from digits_kernel, run right before each product.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -57,14 +61,16 @@ constexpr int BM = 128;
 constexpr int BK = 16;                       // 16-bit elements = 32 B rows
 constexpr int BOX_BYTES = BM * BK * 2;       // 4 KB
 constexpr int ND = 5;                        // digits
-constexpr int STAGES = 5;
+constexpr int STAGES = 4;
 constexpr int STAGE_BYTES = 2 * ND * BOX_BYTES;  // 40 KB
 constexpr int CHUNK_KB = 128 / BK;           // k-blocks per G2 chunk (128 k)
 constexpr int THREADS = 384;
 constexpr int EPI_WARP0 = 4;
 constexpr int NEPI = 8;
 constexpr int TMEM_COLS = 512;               // G0 | G1 | G2 | T
-constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+// running T sums of the drain threads after the ring: [warp][column][lane]
+constexpr int TSUM_BYTES = NEPI * 64 * 32 * 4;
+constexpr int SMEM = STAGES * STAGE_BYTES + TSUM_BYTES + 1024;
 constexpr int kMaxOrder = 8192;              // G1 exactness bound
 // epilogue use of the (then idle) operand ring: staging of the (r, c) stores,
 // then the G2 sums of every epilogue thread
@@ -298,10 +304,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           a[d] = smem_desc_sw32(sa + d * BOX_BYTES);
           b[d] = same ? a[d] : smem_desc_sw32(sa + (ND + d) * BOX_BYTES);
         }
-        // G0, G1 and T do not touch G2: at the first block of a chunk they
-        // go first, so that the drain of the previous chunk's G2 overlaps
-        // them; elsewhere G2 goes first, so that the last block's G2 commit
-        // is followed by that block's other products as well.
+        // G0 and G1 (whole-K accumulators) do not touch the chunked G2 and
+        // T: at the first block of a chunk they go first, so that the drain of
+        // the previous chunk overlaps them; elsewhere G2 and T go first, so
+        // that the last block's chunk commit is followed by that block's G0
+        // and G1 products as well.
         auto issue_rest = [&]() {
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
@@ -310,8 +317,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             mma_f16(g0, a[0] + adv, b[0] + adv, idesc, first);
             mma_f16(g1, a[0] + adv, b[1] + adv, idesc, first);
             mma_f16(g1, a[1] + adv, b[0] + adv, idesc, 1u);
+          }
+        };
+        auto issue_chunked = [&]() {
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+            const uint32_t c_acc = (chunk_first && kk == 0) ? 0u : 1u;
+            mma_f16(g2, a[0] + adv, b[2] + adv, idesc, c_acc);
+            mma_f16(g2, a[1] + adv, b[1] + adv, idesc, 1u);
+            mma_f16(g2, a[2] + adv, b[0] + adv, idesc, 1u);
             // T: small terms first
-            mma_f16(tt, a[0] + adv, b[4] + adv, idesc, first);
+            mma_f16(tt, a[0] + adv, b[4] + adv, idesc, c_acc);
             mma_f16(tt, a[4] + adv, b[0] + adv, idesc, 1u);
             mma_f16(tt, a[1] + adv, b[3] + adv, idesc, 1u);
             mma_f16(tt, a[3] + adv, b[1] + adv, idesc, 1u);
@@ -321,30 +338,20 @@ __global__ void __launch_bounds__(THREADS, 1)
             mma_f16(tt, a[1] + adv, b[2] + adv, idesc, 1u);
             mma_f16(tt, a[2] + adv, b[1] + adv, idesc, 1u);
           }
-        };
-        auto issue_g2 = [&]() {
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-            const uint32_t c_acc = (chunk_first && kk == 0) ? 0u : 1u;
-            mma_f16(g2, a[0] + adv, b[2] + adv, idesc, c_acc);
-            mma_f16(g2, a[1] + adv, b[1] + adv, idesc, 1u);
-            mma_f16(g2, a[2] + adv, b[0] + adv, idesc, 1u);
-          }
           if (chunk_last) mma_commit(g2full);
         };
         if (chunk_first) {
           issue_rest();
-          if (c > 0) {  // the drain has read G2 of the previous chunk
+          if (c > 0) {  // the drain has read G2 and T of the previous chunk
             if (!mbar_wait(g2empty, (uint32_t)(c - 1) & 1u, err, true, wlim)) {
               ok = false;
               break;
             }
             tc_fence_after();
           }
-          issue_g2();
+          issue_chunked();
         } else {
-          issue_g2();
+          issue_chunked();
           issue_rest();
         }
         mma_commit(empty_bar(s));
@@ -363,7 +370,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   int g2acc[64];
 #pragma unroll
   for (int j = 0; j < 64; ++j) g2acc[j] = 0;
+  // this thread's running T sums: [warp][column][lane] after the ring
+  float* tsum = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw)) +
+                                         STAGES * STAGE_BYTES) +
+                (epi ? (warp - EPI_WARP0) * (64 * 32) : 0) + lane;
   if (epi) {
+#pragma unroll
+    for (int j = 0; j < 64; ++j) tsum[j * 32] = 0.0f;
     for (int c = 0; c < NC; ++c) {
       if (!mbar_wait(g2full, (uint32_t)c & 1u, err, true, wlim)) break;
       tc_fence_after();
@@ -371,13 +384,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int q = 0; q < 4; ++q) tmem_ld16(lane_addr + 256 + half * 64 + q * 16, v + q * 16);
       tmem_ld_wait();
-      // the chunk is in registers: free G2 for the next chunk's products first
+#pragma unroll
+      for (int j = 0; j < 64; ++j)  // exact: an integer number of 2^-34 below 2^24
+        g2acc[j] += __float2int_rn(__uint_as_float(v[j]) * 17179869184.0f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tmem_ld16(lane_addr + 384 + half * 64 + q * 16, v + q * 16);
+      tmem_ld_wait();
+      // the chunk is in registers: free G2 and T for the next chunk's products
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(g2empty);
 #pragma unroll
-      for (int j = 0; j < 64; ++j)  // exact: an integer number of 2^-34 below 2^24
-        g2acc[j] += __float2int_rn(__uint_as_float(v[j]) * 17179869184.0f);
+      for (int j = 0; j < 64; ++j) tsum[j * 32] += __uint_as_float(v[j]);  // round to nearest
     }
   }
   const bool ok = mbar_wait(accum_bar, 0u, err, false);
@@ -421,10 +439,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           xml[j] = Xl[m];
         }
       }
-      uint32_t u0[16], u1[16], ut[16];
+      uint32_t u0[16], u1[16];
       tmem_ld16(lane_addr + col, u0);
       tmem_ld16(lane_addr + 128 + col, u1);
-      tmem_ld16(lane_addr + 384 + col, ut);
       tmem_ld_wait();
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
@@ -437,7 +454,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         two_sum(__uint_as_float(u0[j]), __uint_as_float(u1[j]), s, e);
         two_sum(s, g2h * 5.820766091346741e-11f, s, e2);  // 2^-34
         e += e2;
-        two_sum(s, __uint_as_float(ut[j]), s, e2);
+        two_sum(s, tsum[(q * 16 + j) * 32], s, e2);
         e += e2 + g2l * 5.820766091346741e-11f;
         float yh = s + e;
         float yl = e - (yh - s);

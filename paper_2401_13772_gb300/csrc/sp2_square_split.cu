@@ -89,6 +89,10 @@ struct TensorMaps {
 
 using namespace tc;
 
+__device__ __forceinline__ void mbar_arrive_cta(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
 template <int F>
 __global__ void __launch_bounds__(THREADS, 1)
     square_split_kernel(const __grid_constant__ TensorMaps maps, DevBuffers buf,
@@ -401,6 +405,412 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
       for (int kb = s_consumed; kb < issued; ++kb)
         mbar_wait(full_bar(kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, err, false,
+                  kWaitLimitNs / 10);
+    }
+    __syncthreads();
+  }
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+  if (*err && threadIdx.x == 0) {
+    st->status = PROGRESS_ETIMEOUT;
+    st->done = 1;
+  }
+
+  block_sum2(tr, fr, s_scratch);
+  if (threadIdx.x == 0) {
+    buf.partials[2 * blockIdx.x] = tr;
+    buf.partials[2 * blockIdx.x + 1] = fr;
+  }
+  if (!last_cta_arrives(st, gridDim.x, &s_last)) return;
+  double a, b;
+  reduce_partials(buf.partials, gridDim.x, a, b, s_scratch);
+  if (threadIdx.x == 0) {
+    st->ticket = 0u;
+    if (st->status == PROGRESS_ETIMEOUT) {
+      st->done = 1;
+    } else {
+      st->t1 = a;
+      st->t2 = b;
+      st->iter = k_iter + 1;
+      st->phase_iters[kPhaseSplit] += 1;
+      st->x_fp64_valid = want_fp64 ? 1 : 0;
+      st->x_slices_valid = 1;
+      decide(st);
+    }
+    if (st->done && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+  }
+}
+
+// Persistent variant for the two-slice formats (FP16x2, FP16x2F): one CTA per
+// SM walks the upper tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... with
+// barriers and tensor memory kept across tiles, so that the epilogue of one
+// tile overlaps the products of the next. Tensor memory: two leading-group
+// chunk buffers (columns 0..255) and two correction accumulators acc1
+// (256..383 for even, 384..511 for odd tiles of the CTA). At the end of a tile
+// the drain warps fold their FP32 chunk sums into the tile's acc1 buffer
+// (S = w0 sum0 + w1 acc1, written back with tcgen05.st), which frees their
+// registers for the next tile; the rest of that tile's epilogue (branch
+// update, slices at (r, c) and at the mirror, traces) then runs in four
+// 16-column pieces, each taken whenever the next tile's chunk has not arrived
+// yet. A tile's acc1 buffer is handed back to the MMA issuer (acc_empty) after
+// its last piece; the MMA issuer needs it again two tiles later.
+constexpr int P_STAGES = 3;
+constexpr int P_STG_WORDS = 32 * 17;  // per drain warp: 32 rows x 16 columns, stride 17
+constexpr int P_SMEM = 1024 + P_STAGES * 2 * 2 * TILE_BYTES + DRAIN_WARPS * P_STG_WORDS * 4 + 256;
+
+template <int F>
+__global__ void __launch_bounds__(THREADS, 1)
+    square_split_persist_kernel(const __grid_constant__ TensorMaps maps, DevBuffers buf,
+                                unsigned long long cond) {
+  static_assert(!fmt_bf16(F), "the persistent product holds two slices");
+  constexpr int NS = 2;
+  constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_err;
+  __shared__ int s_consumed;
+  __shared__ int s_last;
+  __shared__ double s_scratch[2 * THREADS / 32];
+
+  State* st = buf.st;
+  const int done = __ldcg(&st->done);
+  const int phase = __ldcg(&st->phase);
+  if (done) {
+    if (cond && blockIdx.x == 0 && threadIdx.x == 0)
+      cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+    return;
+  }
+  if (phase != kPhaseSplit) return;  // the FP64-accurate kernel owns this step
+  const int k_iter = __ldcg(&st->iter);
+  const int bit = __ldcg(&st->bit);
+  const int ld = st->ld;
+  const uint64_t wlim = __ldcg(&st->wait_ns);  // bound on the pipeline waits
+  const bool stall = __ldcg(&st->stall_test) != 0 && blockIdx.x == 0;
+  const bool want_fp64 = (st->prec == PROGRESS_MIXED_FP16 || st->prec == PROGRESS_MIXED_BF16) &&
+                         __ldcg(&st->split_stall) >= 1;
+  const int src = k_iter & 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int T = ld / BM;
+  const int tiles = T * (T + 1) / 2;
+  const int my_tiles = (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int KB = ld / BK;
+  const int NC = (KB + CHUNK - 1) / CHUNK;
+
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t stg_base = base + P_STAGES * STAGE_BYTES;
+  const uint32_t bars = stg_base + DRAIN_WARPS * P_STG_WORDS * 4;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (P_STAGES + s); };
+  auto chunk_full = [&](int b) { return bars + 8u * (2 * P_STAGES + b); };
+  auto chunk_empty = [&](int b) { return bars + 8u * (2 * P_STAGES + 2 + b); };
+  auto acc_full = [&](int b) { return bars + 8u * (2 * P_STAGES + 4 + b); };
+  auto acc_empty = [&](int b) { return bars + 8u * (2 * P_STAGES + 6 + b); };
+  const uint32_t mma_done = bars + 8u * (2 * P_STAGES + 8);
+  const uint32_t stall_bar = bars + 8u * (2 * P_STAGES + 9);  // nothing arrives on it
+
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    s_consumed = 0;
+    for (int q = 0; q < P_STAGES; ++q) {
+      mbar_init(full_bar(q), 1);
+      mbar_init(empty_bar(q), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(chunk_full(b), 1);
+      mbar_init(chunk_empty(b), DRAIN_WARPS);
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), DRAIN_WARPS);
+    }
+    mbar_init(mma_done, 1);
+    mbar_init(stall_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  volatile int* err = &s_err;
+
+  int issued = 0;  // producer: k-blocks whose loads were issued (all tiles)
+  if (warp == 0) {
+    if (lane == 0) {
+      int gk = 0;
+      bool ok = true;
+      for (int j = 0; j < my_tiles && ok; ++j) {
+        int I, J;
+        tri_tile((int)blockIdx.x + j * (int)gridDim.x, T, I, J);
+        const int row_a = I * BM, row_b = J * BN;
+        for (int kb = 0; kb < KB; ++kb, ++gk) {
+          const int q = gk % P_STAGES;
+          const uint32_t ph = (uint32_t)(gk / P_STAGES) & 1u;
+          if (!mbar_wait(empty_bar(q), ph ^ 1u, err, true, wlim)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full_bar(q), STAGE_BYTES);
+          const uint32_t sa = base + q * STAGE_BYTES;
+#pragma unroll
+          for (int js = 0; js < NS; ++js) {
+            tma_load_2d(sa + js * TILE_BYTES, &maps.m[src][js], kb * BK, row_a, full_bar(q));
+            tma_load_2d(sa + (NS + js) * TILE_BYTES, &maps.m[src][js], kb * BK, row_b,
+                        full_bar(q));
+          }
+        }
+      }
+      issued = gk;
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16(0, BM, BN);
+      int gk = 0, gc = 0;
+      bool ok = true;
+      for (int j = 0; j < my_tiles && ok; ++j) {
+        const int ab = j & 1;
+        const uint32_t acc1 = tmem + 256u + 128u * ab;
+        if (j >= 2) {  // the epilogue of tile j - 2 has read this acc1 buffer
+          if (!mbar_wait(acc_empty(ab), (uint32_t)((j - 2) >> 1) & 1u, err, true, wlim)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
+        for (int kb = 0; kb < KB; ++kb, ++gk) {
+          const bool chunk_first = (kb % CHUNK) == 0;
+          const bool chunk_last = (kb % CHUNK) == CHUNK - 1 || kb == KB - 1;
+          const int cb = gc & 1;
+          const uint32_t acc0 = tmem + 128u * cb;
+          if (chunk_first) {
+            if (!mbar_wait(chunk_empty(cb), ((uint32_t)(gc >> 1) & 1u) ^ 1u, err, true, wlim)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          // test of the bounded waits: after the first k-block's products, wait
+          // on a barrier that nothing arrives on; it runs out after wlim
+          if (stall && j == 0 && kb == 1 && !mbar_wait(stall_bar, 0u, err, true, wlim)) {
+            ok = false;
+            break;
+          }
+          const int q = gk % P_STAGES;
+          const uint32_t ph = (uint32_t)(gk / P_STAGES) & 1u;
+          if (!mbar_wait(full_bar(q), ph, err, true, wlim)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = base + q * STAGE_BYTES;
+          const uint64_t a0 = smem_desc_sw128(sa), a1 = smem_desc_sw128(sa + TILE_BYTES);
+          const uint64_t b0 = smem_desc_sw128(sa + 2 * TILE_BYTES);
+          const uint64_t b1 = smem_desc_sw128(sa + 3 * TILE_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 32 B per K = 16 step
+            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            const uint32_t chunk_acc = (chunk_first && kk == 0) ? 0u : 1u;
+            mma_f16(acc0, a0 + adv, b0 + adv, idesc, chunk_acc);
+            mma_f16(acc1, a0 + adv, b1 + adv, idesc, first);
+            mma_f16(acc1, a1 + adv, b0 + adv, idesc, 1u);
+          }
+          mma_commit(empty_bar(q));  // frees the stage once these MMAs have read it
+          if (chunk_last) {
+            mma_commit(chunk_full(cb));
+            ++gc;
+          }
+          s_consumed = gk + 1;
+        }
+        if (ok) mma_commit(acc_full(ab));  // the tile's acc1 (and last chunk) complete
+      }
+      mma_commit(mma_done);  // every MMA issued so far is complete
+    }
+    __syncwarp();
+  }
+
+  // ---- drain + epilogue warps: thread owns TMEM lane = tile row and 64
+  // columns; sums the leading-group chunks with round-to-nearest FP32 adds,
+  // folds them into acc1 at the end of a tile and runs the tile's epilogue in
+  // pieces while the next tile's products proceed.
+  double tr = 0.0, fr = 0.0;
+  if (warp >= DRAIN_WARP0) {
+    using W = SliceWeights<F>;
+    const int dw = warp - DRAIN_WARP0;
+    const int quarter = warp & 3;
+    const int half = dw >> 2;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    const bool odd = src != 0;
+    const uint16_t* xs0 = odd ? buf.sl[1][0] : buf.sl[0][0];
+    const uint16_t* xs1 = odd ? buf.sl[1][1] : buf.sl[0][1];
+    uint16_t* const out0 = odd ? buf.sl[0][0] : buf.sl[1][0];
+    uint16_t* const out1 = odd ? buf.sl[0][1] : buf.sl[1][1];
+    double* out64 = odd ? buf.x64[0] : buf.x64[1];
+    const bool df = st->df64 != 0;
+    float* out_hi = reinterpret_cast<float*>(out64);
+    float* out_lo = out_hi + (size_t)ld * ld;
+    uint32_t* stg = reinterpret_cast<uint32_t*>(smem_raw + (stg_base - smem_u32(smem_raw))) +
+                    dw * P_STG_WORDS;
+    float sum0[DCOLS];
+#pragma unroll
+    for (int i = 0; i < DCOLS; ++i) sum0[i] = 0.0f;
+    // the tile whose epilogue is pending (-1: none) and its next piece
+    int p_j = -1, p_piece = 0, p_ra = 0, p_rb = 0;
+
+    // one 16-column piece of the pending epilogue
+    auto do_piece = [&]() {
+      const int r = p_ra + row;
+      const int col = half * DCOLS + p_piece * 16;  // column in the tile
+      const int c0 = p_rb + col;
+      uint32_t m01[16];
+      if (bit) {  // X at the mirror (X symmetric: consecutive lanes read consecutive r)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const size_t m = (size_t)(c0 + i) * ld + r;
+          m01[i] = (uint32_t)xs0[m] | ((uint32_t)xs1[m] << 16);
+        }
+      }
+      uint32_t u[16];
+      tmem_ld16(lane_addr + 256u + 128u * (uint32_t)(p_j & 1) + (uint32_t)col, u);
+      tmem_ld_wait();
+      float trf = 0.0f, frf = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int c = c0 + i;
+        float x = __uint_as_float(u[i]);
+        if (bit)
+          x = 2.0f * join_value<F>((uint16_t)(m01[i] & 0xffffu), (uint16_t)(m01[i] >> 16),
+                                   (uint16_t)0) -
+              x;
+        uint16_t a, b2, c2;
+        split_value_f<F>(x, a, b2, c2);
+        stg[lane * 17 + i] = (uint32_t)a | ((uint32_t)b2 << 16);
+        if (r <= c) {
+          if (r == c) {
+            trf += x;
+            frf += x * x;
+          } else {
+            frf += 2.0f * x * x;
+            const size_t m = (size_t)c * ld + r;  // mirror (c, r)
+            out0[m] = a;
+            out1[m] = b2;
+            if (want_fp64) {
+              if (df) {
+                out_hi[m] = x;
+                out_lo[m] = 0.0f;
+              } else {
+                out64[m] = (double)x;
+              }
+            }
+          }
+          if (want_fp64) {
+            const size_t d = (size_t)r * ld + c;
+            if (df) {
+              out_hi[d] = x;
+              out_lo[d] = 0.0f;
+            } else {
+              out64[d] = (double)x;
+            }
+          }
+        }
+      }
+      tr += (double)trf;
+      fr += (double)frf;
+      // (r, c) slices: 32 rows of 16 columns, two rows per store instruction
+      __syncwarp();
+      const int rbase = p_ra + quarter * 32;
+      const int cc = c0 + (lane & 15);
+#pragma unroll 4
+      for (int it = 0; it < 16; ++it) {
+        const int i = 2 * it + (lane >> 4);
+        if (rbase + i <= cc) {
+          const uint32_t v = stg[i * 17 + (lane & 15)];
+          const size_t d = (size_t)(rbase + i) * ld + cc;
+          out0[d] = (uint16_t)(v & 0xffffu);
+          out1[d] = (uint16_t)(v >> 16);
+        }
+      }
+      __syncwarp();
+      if (++p_piece == DCOLS / 16) {  // the tile's acc1 buffer is free again
+        tc_fence_before();
+        if (lane == 0) mbar_arrive_cta(acc_empty(p_j & 1));
+        p_j = -1;
+      }
+    };
+
+    int gc = 0;
+    bool ok = true;
+    for (int j = 0; j < my_tiles && ok; ++j) {
+      for (int c = 0; c < NC; ++c, ++gc) {
+        const int cb = gc & 1;
+        const uint32_t par = (uint32_t)(gc >> 1) & 1u;
+        // pieces of the pending epilogue while this chunk is not ready yet
+        while (p_j >= 0 && __shfl_sync(0xffffffffu, (int)mbar_test_wait(chunk_full(cb), par), 0) == 0)
+          do_piece();
+        if (!mbar_wait(chunk_full(cb), par, err, true, wlim)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // 32 columns at a time (register budget), the buffer freed after the last
+#pragma unroll
+        for (int q = 0; q < DCOLS / 32; ++q) {
+          float v[32];
+          tmem_ld32(lane_addr + 128u * cb + half * DCOLS + q * 32, v);
+          tmem_ld_wait();
+          if (q == DCOLS / 32 - 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cta(chunk_empty(cb));
+          }
+#pragma unroll
+          for (int i = 0; i < 32; ++i) sum0[q * 32 + i] += v[i];
+        }
+      }
+      if (!ok) break;
+      while (p_j >= 0) do_piece();
+      if (!mbar_wait(acc_full(j & 1), (uint32_t)(j >> 1) & 1u, err, true, wlim)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      // S = w0 sum0 + w1 acc1, written back over acc1 (this thread's row and columns)
+      const uint32_t a1 = lane_addr + 256u + 128u * (uint32_t)(j & 1) + half * DCOLS;
+#pragma unroll
+      for (int q = 0; q < DCOLS / 16; ++q) {
+        uint32_t u[16];
+        tmem_ld16(a1 + q * 16, u);
+        tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          u[i] = __float_as_uint(sum0[q * 16 + i] * W::w0 + __uint_as_float(u[i]) * W::w1);
+          sum0[q * 16 + i] = 0.0f;
+        }
+        tmem_st16(a1 + q * 16, u);
+      }
+      tmem_st_wait();
+      int I, J;
+      tri_tile((int)blockIdx.x + j * (int)gridDim.x, T, I, J);
+      p_j = j;
+      p_piece = 0;
+      p_ra = I * BM;
+      p_rb = J * BN;
+    }
+    if (ok)
+      while (p_j >= 0) do_piece();
+  }
+
+  // every MMA is complete before tensor memory is released (the MMA thread
+  // always commits mma_done; this wait does not abort early)
+  mbar_wait(mma_done, 0u, err, false);
+  tc_fence_after();
+  tc_fence_before();
+  __syncthreads();
+  if (*err) {
+    // failure path: let TMA copies still in flight land before the CTA exits
+    if (threadIdx.x == 0) {
+      for (int g = s_consumed; g < issued; ++g)
+        mbar_wait(full_bar(g % P_STAGES), (uint32_t)(g / P_STAGES) & 1u, err, false,
                   kWaitLimitNs / 10);
     }
     __syncthreads();
@@ -899,6 +1309,27 @@ cudaError_t launch_square_split(const DevBuffers& b, const SolveParams& p,
       SP2_SQP(kFP16x2)
       SP2_SQP(kBF16x3)
 #undef SP2_SQP
+      default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  if (!fmt_bf16(p.slice_fmt)) {
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = nsm < tiles ? nsm : tiles;  // one CTA per SM, never more than tiles
+    switch (p.slice_fmt) {
+#define SP2_SQPER(F)                                                                       \
+  case F:                                                                                  \
+    cudaFuncSetAttribute(square_split_persist_kernel<F>,                                   \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM);            \
+    square_split_persist_kernel<F><<<grid, THREADS, P_SMEM, s>>>(maps, b, cond_handle);    \
+    break;
+      SP2_SQPER(kFP16x2)
+      SP2_SQPER(kFP16x2F)
+#undef SP2_SQPER
       default:
         return cudaErrorInvalidValue;
     }

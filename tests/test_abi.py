@@ -158,7 +158,8 @@ def test_argument_errors_before_any_device_work(lib):
     assert b"tau" in lib.progress_last_error()
     o.prec, o.slice_fixed = _lib.FP32_SPLIT, 1
     assert lib.progress_sp2_dense_ex(P(16), 8, 4, 1e-9, P(32), ctypes.byref(o), None, None) == _lib.EINVAL
-    assert lib.progress_gershgorin_bounds(P(16), 0, P(32), None) == _lib.EINVAL
+    assert lib.progress_gershgorin_bounds(P(16), 0, P(32), P(40), None) == _lib.EINVAL
+    assert lib.progress_gershgorin_bounds(P(16), 4, P(32), None, None) == _lib.EINVAL
     assert b"n < 1" in lib.progress_last_error()
     # n = 0 is a no-op
     info = _lib.Info()

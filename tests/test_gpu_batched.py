@@ -4,10 +4,12 @@ Each instance is compared element by element with the oracle's plain FP64 SP2
 (itself pinned to the spectral projector on the CPU). The batched solver runs
 split products with FP32 accumulation and no FP64 refinement, so its error is
 that of FP32-level SP2: unit round-off u of the split products (2^-22: the
-operand split for fp16 hi+lo, the FP32 accumulation for bf16) amplified by the inverse relative gap
-(gap / (emax - emin)) of each instance. The gate is max |D - D_ref| <=
-0.2 u / relgap + 1e-6 per instance (the measured constant is <= 0.04), and
-|Tr D - Nocc| <= 4e-6 n.
+operand split for fp16 hi+lo; the FP32 accumulation for bf16) amplified by the
+inverse relative gap (gap / (emax - emin)) of each instance. The gate is
+max |D - D_ref| <= min(0.2 u / relgap + 1e-6, 1e-2) per instance -- the
+round-off-over-gap estimate with a fixed ceiling; measured over all 4000 parts
+of the benchmark batch (FP16x2): median 8.8e-5, 99th percentile 5.2e-4,
+largest 7.4e-3 at relgap 1.4e-6 -- and |Tr D - Nocc| <= 4e-6 n.
 """
 
 import numpy as np
@@ -19,15 +21,16 @@ from workloads import batch_instance, cube_hamiltonian
 pytestmark = pytest.mark.gpu
 
 # FP32 accumulation bounds both encodings (the bf16 split carries 24 bits but
-# accumulates all six products in one FP32 accumulator)
+# accumulates in FP32)
 UNIT = {"fp32_split": 2.0 ** -22, "fp32_split_bf16": 2.0 ** -22}
+CEILING = 1e-2  # fixed ceiling of the per-instance gate
 
 
 def gate(H, nocc, prec):
     w = np.linalg.eigvalsh(H)
     emin, emax = oracle.gershgorin_bounds(H)
     relgap = (w[nocc] - w[nocc - 1]) / (emax - emin)
-    return 0.2 * UNIT[prec] / relgap + 1e-6
+    return min(0.2 * UNIT[prec] / relgap + 1e-6, CEILING)
 
 
 @pytest.fixture(scope="module")

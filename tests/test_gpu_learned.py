@@ -214,5 +214,5 @@ def test_trained_predictor_saves_iterations(L):
             ref = oracle.sp2_plain(H, no, 1e-10)["D"]
             w = np.linalg.eigvalsh(H)
             emin, emax = oracle.gershgorin_bounds(H)
-            g = 0.2 * 2.0 ** -22 * (emax - emin) / (w[no] - w[no - 1]) + 1e-6
+            g = min(0.2 * 2.0 ** -22 * (emax - emin) / (w[no] - w[no - 1]) + 1e-6, 1e-2)
             assert np.abs(Dl[o:o + k * k].reshape(k, k) - ref).max() <= g

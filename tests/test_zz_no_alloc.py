@@ -1,9 +1,9 @@
 """The allocation-free FP64 entry point, through the C ABI, against the
-regular one. It serves callers that cannot allocate device memory (a stream
-capture in global mode, a device already owned by another memory pool, a
-time-stepping loop that must not pay allocation latency): its work space is a
-fixed device array inside the library, so two calls in a row must not leak
-state from one into the other."""
+regular one. It serves callers that cannot allocate device memory (a device
+already owned by the application's own memory pool, a time-stepping loop that
+must not pay allocation latency): its work space is a fixed device array
+inside the library, so two calls in a row must not leak state from one into
+the other."""
 
 import ctypes
 
