@@ -167,8 +167,8 @@ progress_status_t ensure_buffers(Workspace* w, int ld, bool need_x64, int nslice
     for (int i = 0; i < ns && e == cudaSuccess; ++i)
       e = cudaMalloc(&w->buf.sl[k][i], elems * sizeof(uint16_t));
   }
-  for (int d = 0; d < 5 && dg && e == cudaSuccess; ++d)
-    e = cudaMalloc(&w->buf.dg[d], elems * sizeof(uint16_t));
+  if (dg && e == cudaSuccess) e = cudaMalloc(&w->buf.dg[0], 4 * elems * sizeof(uint16_t));
+  if (dg && e == cudaSuccess) e = cudaMalloc(&w->buf.dg[4], elems * sizeof(uint16_t));
   int maxp = sp2::fp64_tile_count(new_ld);
   if (sp2::df64_tile_count(new_ld) > maxp) maxp = sp2::df64_tile_count(new_ld);
   const int sp = sp2::split_tile_count(new_ld);

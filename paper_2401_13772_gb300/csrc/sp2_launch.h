@@ -14,7 +14,10 @@ struct DevBuffers {
   State* st;
   double* x64[2];        // FP64 ping-pong iterates, ld x ld
   uint16_t* sl[2][3];    // slice ping-pong sets, ld x ld each
-  uint16_t* dg[5];       // BF16 fixed-point digits of the iterate (digit products), ld x ld
+  uint16_t* dg[5];       // BF16 fixed-point digits of the iterate (digit products):
+                         // dg[0] holds digits 0..3 interleaved, ld x 4 ld (row r, column
+                         // 64 g + 16 d + i = digit d of element 16 g + i); dg[4] holds
+                         // digit 4, ld x ld; dg[1..3] are not used
   uint8_t* tflags[2];    // thresholded SP2: per 128 x 128 tile of slice set k, 1 if it may
                          // hold a non-zero ((ld/128)^2 bytes each)
   double* partials;      // per-CTA partial traces (2 doubles per CTA)

@@ -34,8 +34,10 @@
 // and X' is written back as double-float planes.
 //
 // Roles (one CTA per 128 x 128 upper-triangle tile, 384 threads):
-//   warp 0 lane 0 : TMA producer, 5 + 5 digit boxes of 128 x 16 (32 B rows,
-//                   32 B swizzle) per stage, four stages
+//   warp 0 lane 0 : TMA producer; per stage (16 k) and operand one 128 x 64
+//                   box of the interleaved plane (digits 0..3 of the 16 k in
+//                   one 128 B row, 128 B swizzle) and one 128 x 16 box of
+//                   digit 4 (32 B rows, 32 B swizzle); four stages
 //   warp 1 lane 0 : MMA issuer (kind::f16 with BF16 operands, M = N = 128,
 //                   K = 16); per stage it issues the G2 and T products first,
 //                   so that at the end of a chunk the drain can read them
@@ -59,7 +61,8 @@ using namespace tc;
 
 constexpr int BM = 128;
 constexpr int BK = 16;                       // 16-bit elements = 32 B rows
-constexpr int BOX_BYTES = BM * BK * 2;       // 4 KB
+constexpr int BOX_BYTES = BM * BK * 2;       // 4 KB: one digit of a 128 x 16 operand
+constexpr int IBOX_BYTES = 4 * BOX_BYTES;    // 16 KB: digits 0..3 interleaved
 constexpr int ND = 5;                        // digits
 constexpr int STAGES = 4;
 constexpr int STAGE_BYTES = 2 * ND * BOX_BYTES;  // 40 KB
@@ -80,7 +83,8 @@ static_assert(STAGING_BYTES <= G2S_OFFSET, "staging overlaps the G2 sums");
 static_assert(G2S_OFFSET + NEPI * 64 * 32 * 4 <= STAGES * STAGE_BYTES, "ring too small");
 
 struct OzMaps {
-  CUtensorMap d[ND];  // digit planes, 16 x 128 boxes
+  CUtensorMap p0;  // digits 0..3 interleaved (ld x 4 ld), 64 x 128 boxes, 128 B swizzle
+  CUtensorMap p4;  // digit 4 (ld x ld), 16 x 128 boxes, 32 B swizzle
 };
 
 // Shared-memory matrix descriptor: K-major operand, 32 B swizzle (8-row atoms
@@ -176,9 +180,15 @@ __global__ void __launch_bounds__(256) digits_kernel(DevBuffers buf, int ld) {
           w[s][e >> 1] = bits;
       }
     }
+    // element (r, k) = 4 q .. 4 q + 3 of the plane: digits 0..3 go to the
+    // interleaved plane at row r, column 64 (k / 16) + 16 d + k % 16
+    const size_t e0 = 4 * q;
+    const size_t r = e0 / (size_t)ld, k = e0 % (size_t)ld;
+    uint16_t* rowp = buf.dg[0] + r * (size_t)(4 * ld) + (k >> 4) * 64 + (k & 15);
 #pragma unroll
-    for (int s = 0; s < ND; ++s)
-      reinterpret_cast<uint2*>(buf.dg[s])[q] = make_uint2(w[s][0], w[s][1]);
+    for (int s = 0; s < ND - 1; ++s)
+      *reinterpret_cast<uint2*>(rowp + 16 * s) = make_uint2(w[s][0], w[s][1]);
+    reinterpret_cast<uint2*>(buf.dg[4])[q] = make_uint2(w[ND - 1][0], w[ND - 1][1]);
   }
 }
 
@@ -220,7 +230,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int T = ld / BM;
   int I, J;
-  tri_tile(blockIdx.x, T, I, J);
+  band_tile<8>(blockIdx.x, T, I, J);
   const int row_a = I * BM, row_b = J * BM;
   const bool same = (I == J);
 
@@ -265,12 +275,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
         if (!mbar_wait(empty_bar(s), ph ^ 1u, err, true, wlim)) break;
         mbar_expect_tx(full_bar(s), stage_bytes);
+        // stage: A interleaved | B interleaved | A digit 4 | B digit 4
         const uint32_t sa = base + s * STAGE_BYTES;
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-          tma_load_2d(sa + d * BOX_BYTES, &maps.d[d], kb * BK, row_a, full_bar(s));
-          if (!same)
-            tma_load_2d(sa + (ND + d) * BOX_BYTES, &maps.d[d], kb * BK, row_b, full_bar(s));
+        tma_load_2d(sa, &maps.p0, kb * 64, row_a, full_bar(s));
+        tma_load_2d(sa + 2 * IBOX_BYTES, &maps.p4, kb * BK, row_a, full_bar(s));
+        if (!same) {
+          tma_load_2d(sa + IBOX_BYTES, &maps.p0, kb * 64, row_b, full_bar(s));
+          tma_load_2d(sa + 2 * IBOX_BYTES + BOX_BYTES, &maps.p4, kb * BK, row_b, full_bar(s));
         }
       }
     }
@@ -279,83 +290,104 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_f16(1, BM, BM);  // BF16 x BF16 -> FP32
       const uint32_t g0 = tmem, g1 = tmem + 128, g2 = tmem + 256, tt = tmem + 384;
+      // operand descriptors of stage s: digit d < 4 of the interleaved box is
+      // the 32 B slice at 32 d of every 128 B swizzled row (its descriptor
+      // starts 32 d bytes in); digit 4 has its own box
+      auto descs = [&](int s, uint64_t* a, uint64_t* b) {
+        const uint32_t sa = base + s * STAGE_BYTES;
+        const uint64_t a0 = smem_desc_sw128(sa), b0 = smem_desc_sw128(sa + IBOX_BYTES);
+#pragma unroll
+        for (int d = 0; d < ND - 1; ++d) {
+          a[d] = a0 + (uint64_t)((d * 32) >> 4);
+          b[d] = same ? a[d] : b0 + (uint64_t)((d * 32) >> 4);
+        }
+        a[ND - 1] = smem_desc_sw32(sa + 2 * IBOX_BYTES);
+        b[ND - 1] = same ? a[ND - 1] : smem_desc_sw32(sa + 2 * IBOX_BYTES + BOX_BYTES);
+      };
+      // G0 and G1: whole-K accumulators (exact); the first block overwrites
+      auto issue_rest = [&](int kb, const uint64_t* a, const uint64_t* b) {
+        const uint32_t first = kb == 0 ? 0u : 1u;
+        mma_f16(g0, a[0], b[0], idesc, first);
+        mma_f16(g1, a[0], b[1], idesc, first);
+        mma_f16(g1, a[1], b[0], idesc, 1u);
+      };
+      // G2 and T: accumulated per 128-k chunk (the chunk's first block
+      // overwrites); the chunk's last block commits them to the drain
+      auto issue_chunked = [&](int kb, const uint64_t* a, const uint64_t* b) {
+        const uint32_t c_acc = (kb % CHUNK_KB) == 0 ? 0u : 1u;
+        mma_f16(g2, a[0], b[2], idesc, c_acc);
+        mma_f16(g2, a[1], b[1], idesc, 1u);
+        mma_f16(g2, a[2], b[0], idesc, 1u);
+        // T: small terms first
+        mma_f16(tt, a[0], b[4], idesc, c_acc);
+        mma_f16(tt, a[4], b[0], idesc, 1u);
+        mma_f16(tt, a[1], b[3], idesc, 1u);
+        mma_f16(tt, a[3], b[1], idesc, 1u);
+        mma_f16(tt, a[2], b[2], idesc, 1u);
+        mma_f16(tt, a[0], b[3], idesc, 1u);
+        mma_f16(tt, a[3], b[0], idesc, 1u);
+        mma_f16(tt, a[1], b[2], idesc, 1u);
+        mma_f16(tt, a[2], b[1], idesc, 1u);
+        if ((kb % CHUNK_KB) == CHUNK_KB - 1 || kb == KB - 1) mma_commit(g2full);
+      };
+      auto wait_full = [&](int kb) {
+        return mbar_wait(full_bar(kb % STAGES), (uint32_t)(kb / STAGES) & 1u, err, true, wlim);
+      };
       bool ok = true;
-      for (int kb = 0; kb < KB && ok; ++kb) {
+      for (int kb = 0; kb < KB && ok;) {
         const int c = kb / CHUNK_KB;
-        const bool chunk_first = (kb % CHUNK_KB) == 0;
-        const bool chunk_last = (kb % CHUNK_KB) == CHUNK_KB - 1 || kb == KB - 1;
-        const int s = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        uint64_t a[ND], b[ND];
+        if (c > 0 && (kb % CHUNK_KB) == 0) {
+          // chunk boundary: G2 and T may be reused only after the drain has
+          // read the previous chunk. Issue G0 and G1 of up to STAGES - 1
+          // blocks first (the tensor core works while the drain reads), then
+          // wait, then their G2 and T products.
+          int L = STAGES - 1;
+          if (L > KB - kb) L = KB - kb;
+          if (L > CHUNK_KB) L = CHUNK_KB;
+          for (int l = 0; l < L; ++l) {
+            if (!wait_full(kb + l)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            descs((kb + l) % STAGES, a, b);
+            issue_rest(kb + l, a, b);
+          }
+          if (!ok) break;
+          if (!mbar_wait(g2empty, (uint32_t)(c - 1) & 1u, err, true, wlim)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int l = 0; l < L; ++l) {
+            descs((kb + l) % STAGES, a, b);
+            issue_chunked(kb + l, a, b);
+            mma_commit(empty_bar((kb + l) % STAGES));  // frees the stage once read
+            s_consumed = kb + l + 1;
+          }
+          kb += L;
+          continue;
+        }
         // test of the bounded waits: after the first k-block's products, wait
         // on a barrier that nothing arrives on; it runs out after wlim
         if (stall && kb == 1 && !mbar_wait(stall_bar, 0u, err, true, wlim)) {
           ok = false;
           break;
         }
-        if (!mbar_wait(full_bar(s), ph, err, true, wlim)) {
+        if (!wait_full(kb)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t sa = base + s * STAGE_BYTES;
-        uint64_t a[ND], b[ND];
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-          a[d] = smem_desc_sw32(sa + d * BOX_BYTES);
-          b[d] = same ? a[d] : smem_desc_sw32(sa + (ND + d) * BOX_BYTES);
-        }
-        // G0 and G1 (whole-K accumulators) do not touch the chunked G2 and
-        // T: at the first block of a chunk they go first, so that the drain of
-        // the previous chunk overlaps them; elsewhere G2 and T go first, so
-        // that the last block's chunk commit is followed by that block's G0
-        // and G1 products as well.
-        auto issue_rest = [&]() {
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 32 B per K = 16 step
-            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-            mma_f16(g0, a[0] + adv, b[0] + adv, idesc, first);
-            mma_f16(g1, a[0] + adv, b[1] + adv, idesc, first);
-            mma_f16(g1, a[1] + adv, b[0] + adv, idesc, 1u);
-          }
-        };
-        auto issue_chunked = [&]() {
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-            const uint32_t c_acc = (chunk_first && kk == 0) ? 0u : 1u;
-            mma_f16(g2, a[0] + adv, b[2] + adv, idesc, c_acc);
-            mma_f16(g2, a[1] + adv, b[1] + adv, idesc, 1u);
-            mma_f16(g2, a[2] + adv, b[0] + adv, idesc, 1u);
-            // T: small terms first
-            mma_f16(tt, a[0] + adv, b[4] + adv, idesc, c_acc);
-            mma_f16(tt, a[4] + adv, b[0] + adv, idesc, 1u);
-            mma_f16(tt, a[1] + adv, b[3] + adv, idesc, 1u);
-            mma_f16(tt, a[3] + adv, b[1] + adv, idesc, 1u);
-            mma_f16(tt, a[2] + adv, b[2] + adv, idesc, 1u);
-            mma_f16(tt, a[0] + adv, b[3] + adv, idesc, 1u);
-            mma_f16(tt, a[3] + adv, b[0] + adv, idesc, 1u);
-            mma_f16(tt, a[1] + adv, b[2] + adv, idesc, 1u);
-            mma_f16(tt, a[2] + adv, b[1] + adv, idesc, 1u);
-          }
-          if (chunk_last) mma_commit(g2full);
-        };
-        if (chunk_first) {
-          issue_rest();
-          if (c > 0) {  // the drain has read G2 and T of the previous chunk
-            if (!mbar_wait(g2empty, (uint32_t)(c - 1) & 1u, err, true, wlim)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-          }
-          issue_chunked();
-        } else {
-          issue_chunked();
-          issue_rest();
-        }
-        mma_commit(empty_bar(s));
+        descs(kb % STAGES, a, b);
+        // G2 and T first, so that a chunk's last commit is followed by that
+        // block's G0 and G1 products as well
+        issue_chunked(kb, a, b);
+        issue_rest(kb, a, b);
+        mma_commit(empty_bar(kb % STAGES));
         s_consumed = kb + 1;
+        ++kb;
       }
       mma_commit(accum_bar);  // every MMA issued so far is complete -> epilogue
     }
@@ -563,13 +595,22 @@ bool encode_oz_maps(const DevBuffers& b, int ld, OzMaps* maps) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = oz_encoder();
   if (!enc) return false;
   memset(maps, 0, sizeof *maps);
-  for (int d = 0; d < ND; ++d) {
-    if (!b.dg[d]) return false;
+  if (!b.dg[0] || !b.dg[4]) return false;
+  cuuint32_t estr[2] = {1, 1};
+  {  // digits 0..3 interleaved: ld rows of 4 ld elements, boxes of 64 x 128
+    cuuint64_t dims[2] = {(cuuint64_t)(4 * ld), (cuuint64_t)ld};
+    cuuint64_t strides[1] = {(cuuint64_t)(4 * ld) * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)BM};
+    if (enc(&maps->p0, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)b.dg[0], dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  {  // digit 4: ld x ld, boxes of 16 x 128
     cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ld};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
     cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
-    cuuint32_t estr[2] = {1, 1};
-    if (enc(&maps->d[d], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)b.dg[d], dims, strides, box,
+    if (enc(&maps->p4, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)b.dg[4], dims, strides, box,
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
@@ -583,8 +624,7 @@ int oz_max_order() { return kMaxOrder; }
 
 cudaError_t launch_digits(const DevBuffers& b, int ld, cudaStream_t s) {
   if (ld % BM || ld > kMaxOrder) return cudaErrorInvalidValue;
-  for (int d = 0; d < ND; ++d)
-    if (!b.dg[d]) return cudaErrorInvalidValue;
+  if (!b.dg[0] || !b.dg[4]) return cudaErrorInvalidValue;
   const size_t n4 = (size_t)ld * ld / 4;
   int blocks = (int)((n4 + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;

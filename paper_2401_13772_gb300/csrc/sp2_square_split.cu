@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       for (int j = 0; j < my_tiles && ok; ++j) {
         int I, J;
-        tri_tile((int)blockIdx.x + j * (int)gridDim.x, T, I, J);
+        band_tile<8>((int)blockIdx.x + j * (int)gridDim.x, T, I, J);
         const int row_a = I * BM, row_b = J * BN;
         for (int kb = 0; kb < KB; ++kb, ++gk) {
           const int q = gk % P_STAGES;
@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       tmem_st_wait();
       int I, J;
-      tri_tile((int)blockIdx.x + j * (int)gridDim.x, T, I, J);
+      band_tile<8>((int)blockIdx.x + j * (int)gridDim.x, T, I, J);
       p_j = j;
       p_piece = 0;
       p_ra = I * BM;

@@ -211,5 +211,35 @@ __device__ __forceinline__ void tri_tile(int t, int T, int& I, int& J) {
   J = i + (t - (i * T - i * (i - 1) / 2));
 }
 
+// Upper tile t (0 <= t < T (T + 1) / 2) in an L2-friendly order: row blocks
+// are taken in bands of G; a band walks its column blocks J = band start ..
+// T - 1, and for each J its row blocks I <= J. Tiles that run at the same time
+// then share few operand panels (G row panels and the current column panels)
+// instead of a whole row of the triangle's column panels.
+template <int G>
+__device__ __forceinline__ void band_tile(int t, int T, int& I, int& J) {
+  int b0 = 0;
+  for (;;) {
+    const int g = T - b0 < G ? T - b0 : G;       // rows in this band
+    const int tri = g * (g + 1) / 2;             // J in [b0, b0 + g): I in [b0, J]
+    const int count = tri + g * (T - b0 - g);    // J >= b0 + g: all g rows
+    if (t < count) {
+      if (t < tri) {  // triangular head of the band
+        int j = 0;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        J = b0 + j;
+        I = b0 + (t - j * (j + 1) / 2);
+      } else {
+        const int u = t - tri;
+        J = b0 + g + u / g;
+        I = b0 + u % g;
+      }
+      return;
+    }
+    t -= count;
+    b0 += g;
+  }
+}
+
 }  // namespace tc
 }  // namespace sp2
