@@ -197,6 +197,133 @@ __global__ void __launch_bounds__(kEwThreads) x0_kernel(const double* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// X0 as double-float planes (hi, lo floats) without FP64 arithmetic, for the
+// solves whose FP64-accurate products keep the iterate as double-float (digit
+// and double-float products). GB300 issues FP64 arithmetic and FP64 <-> FP32
+// conversions at a small fraction of the FP32 rate, so the plain X0 kernel was
+// bound by them (1.2 ms at n = 8192); here each entry of H is cut into two
+// floats with integer operations and the map is evaluated in double-float
+// arithmetic (about 2^-46 relative accuracy, below the 2^-40 absolute error
+// of one digit product).
+
+// x = hi + lo with hi the 24-bit truncation of x and lo the rest rounded to 24
+// bits (|x - hi - lo| <= 2^-48 |x|); zero stays zero. Entries outside
+// [2^-74, 2^127] in magnitude take an FP64 path.
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  if ((u << 1) == 0ull) {
+    hi = 0.0f;
+    lo = 0.0f;
+    return;
+  }
+  const int e = (int)((u >> 52) & 0x7ffull);
+  if (e < 949 || e > 1150) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+    return;
+  }
+  const unsigned int sign = (unsigned int)(u >> 63) << 31;
+  const unsigned long long m = u & 0xfffffffffffffull;
+  hi = __uint_as_float(sign | ((unsigned int)(e - 896) << 23) | (unsigned int)(m >> 29));
+  const float scale = __uint_as_float((unsigned int)(e - 948) << 23);  // 2^(e - 1075)
+  const float l = __uint2float_rn((unsigned int)(m & 0x1fffffffull)) * scale;
+  lo = sign ? -l : l;
+}
+
+__device__ __forceinline__ void fast_two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float v = s - a;
+  e = (a - (s - v)) + (b - v);
+}
+
+// (ah + al) (bh + bl) in double-float
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& rh,
+                                       float& rl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  fast_two_sum_f(p, e, rh, rl);
+}
+
+// acc += (xh + xl) in double-float
+__device__ __forceinline__ void df_acc(float& ch, float& cl, float xh, float xl) {
+  float s, t;
+  two_sum_f(ch, xh, s, t);
+  t += cl + xl;
+  fast_two_sum_f(s, t, ch, cl);
+}
+
+__global__ void __launch_bounds__(kEwThreads) x0_df_kernel(const double* __restrict__ H,
+                                                            State* st, float* __restrict__ Xf,
+                                                            double* __restrict__ partials) {
+  __shared__ double scratch[2 * kEwThreads / 32];
+  __shared__ int s_last;
+  const int64_t n = st->n;
+  const int ld = st->ld;
+  const size_t plane = (size_t)ld * ld;
+  // emax and 1 / (emax - emin) as double-float pairs (a handful of FP64
+  // operations per thread)
+  const double emax = st->emax;
+  const double inv_w = 1.0 / (st->emax - st->emin);
+  float eh, el, ih, il;
+  eh = (float)emax;
+  el = (float)(emax - (double)eh);
+  ih = (float)inv_w;
+  il = (float)(inv_w - (double)ih);
+  float trh = 0.0f, trl = 0.0f, frh = 0.0f, frl = 0.0f;
+  for (int64_t r = blockIdx.x; r < ld; r += gridDim.x) {
+    for (int64_t c = threadIdx.x; c < ld; c += kEwThreads) {
+      const size_t idx = (size_t)r * ld + c;
+      float xh = 0.0f, xl = 0.0f;
+      if (r < n && c < n) {
+        float hh, hl;
+        split_df(H[r * n + c], hh, hl);
+        if (r == c) {  // emax - h
+          float s, t;
+          two_sum_f(eh, -hh, s, t);
+          t += el - hl;
+          fast_two_sum_f(s, t, hh, hl);
+          df_mul(hh, hl, ih, il, xh, xl);
+          df_acc(trh, trl, xh, xl);
+        } else {
+          df_mul(-hh, -hl, ih, il, xh, xl);
+        }
+        // x^2 in double-float (xl^2 is below the pair's precision)
+        const float p = xh * xh;
+        const float e = fmaf(xh, xh, -p) + 2.0f * xh * xl;
+        df_acc(frh, frl, p, e);
+      }
+      Xf[idx] = xh;
+      Xf[plane + idx] = xl;
+    }
+  }
+  double tr = (double)trh + (double)trl, fr = (double)frh + (double)frl;
+  block_sum2(tr, fr, scratch);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = tr;
+    partials[2 * blockIdx.x + 1] = fr;
+  }
+  if (!last_cta_arrives(st, gridDim.x, &s_last)) return;
+  double a, b;
+  reduce_partials(partials, gridDim.x, a, b, scratch);
+  if (threadIdx.x == 0) {
+    st->t1 = a;
+    st->t2 = b;
+    st->iter = 0;
+    st->x_fp64_valid = 1;
+    st->x_slices_valid = 0;
+    st->ticket = 0u;
+    decide(st);
+  }
+}
+
 // D (n x n, leading dim n) <- the current iterate, from FP64 if it is stored
 // that way, else from its slices.
 template <int F>
@@ -261,6 +388,11 @@ cudaError_t launch_x0(const double* H, const DevBuffers& b, const SolveParams& p
   const int write_slices = split_first ? 1 : 0;
   int blocks = ew_blocks(p.ld);
   if (blocks > b.max_partials) blocks = b.max_partials;
+  if (write_fp64 && p.df64) {  // double-float planes, no FP64 arithmetic per entry
+    x0_df_kernel<<<blocks, kEwThreads, 0, s>>>(H, b.st, reinterpret_cast<float*>(b.x64[0]),
+                                               b.partials);
+    return cudaGetLastError();
+  }
   Slices S;
   for (int i = 0; i < 3; ++i) S.s[i] = b.sl[0][i];
   switch (p.slice_fmt) {
