@@ -46,11 +46,15 @@ OZ_KERNEL = ("square_oz_kernel (BF16 digit products, tcgen05; time includes digi
              "traffic is square_oz_kernel's)")
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands, keyed by (kernel, n); see profiles/.
+SPLIT_KERNEL = "square_split_persist_kernel (tcgen05, FP16x2)"
 NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200,
                ("square_df64_kernel (double-float, FP32 pipe)", 4096): 521512448,
                ("square_split_kernel (tcgen05)", 4096): 155314688,
                (OZ_KERNEL, 4096): 658146304}
 NOMINAL_FP64_TFLOPS = 1.25
+# FP64 ceiling of this GPU: cuBLAS DGEMM 8192^3 (torch.matmul, float64) measured
+# on GB300 at 1.10 TFLOP/s (best of 5, CUDA events); used for the FP64 roofline
+MEASURED_DGEMM_TFLOPS = 1.10
 # FP32-class (all split) solves: no tolerance is stated for them. Gate used:
 # max |D - D_ref| <= 1e-4 and |Tr D - Nocc| <= 4 n 2^-22 (the split phase stops
 # on its round-off floor, about n times the slices' 2^-22 resolution)
@@ -575,7 +579,7 @@ def run_learned(args):
         Y = P.predict(L.features(ev))
         return L.batched_solve(ev, nocc, bounds=L.predicted_bounds(Y, gersh, margin))
     lb, t_lb = timed(learned_solve)
-    lj, t_lj = timed(lambda: L.solve_learned(P, ev, nocc, gersh, margin, judge_delta=0.5))
+    lj, t_lj = timed(lambda: L.solve_learned(P, ev, nocc, gersh, margin, judge_delta=0.5, tau=2.0))
     # D of a sample of evaluation instances against the oracle (plain FP64 SP2):
     # per instance gate min(0.2 2^-22 / relgap + 1e-6, 1e-2) of the FP32-class
     # split products
@@ -1087,7 +1091,7 @@ def main():
     flops_alg = float(n) * n * (n + 1)  # one symmetric square, upper triangle
     peaks, peak_src = load_peaks()
     bf16_peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
-    fp64_peak = bf16_peak * (NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS)
+    fp64_peak = MEASURED_DGEMM_TFLOPS
     loop_mean = statistics.mean(loop_ms)
     phases = qinfo["phase_iters"]
     n_fp64 = phases[0] + phases[2]
@@ -1100,7 +1104,8 @@ def main():
                 "peak_source": note,
                 "flops_per_launch": flops_alg, "avg_launch_ms": ms}
 
-    note64 = f"fp64: {peak_src} bf16 burst x nominal fp64/bf16 ratio (1.25/2250)"
+    note64 = ("fp64: measured cuBLAS DGEMM 8192^3 on this GPU (1.10 TFLOP/s; the kernel does "
+              "the upper triangle, so its algorithmic rate is its FP64 work rate)")
     note16 = f"fp16/bf16 dense, {peak_src} burst"
     # double-float products: FP32 pipe, 152 SMs x 128 lanes x max SM clock,
     # DF_OPS FP32 instructions per double-float multiply-add (2 flops)
@@ -1117,6 +1122,8 @@ def main():
                f"FP64-accurate product")
     else:
         k64, p64, n64, b64 = ("square_fp64_kernel (FP64 DMMA)", fp64_peak, note64, "tensor")
+    split_kernel = (SPLIT_KERNEL if "bf16" not in args.prec
+                    else "square_split_kernel (tcgen05, BF16x3)")
     split_ms = None
     if n_split > 0:
         if n_fp64 == 0:
@@ -1134,10 +1141,10 @@ def main():
         fp64_ms = (loop_mean - n_split * (split_ms or 0.0)) / n_fp64
     if fp64_ms is not None and (split_ms is None or n_fp64 * fp64_ms >= n_split * split_ms):
         roofline = roof(k64, fp64_ms, p64, n64, b64)
-        secondary = roof("square_split_kernel (tcgen05)", split_ms, bf16_peak, note16) \
+        secondary = roof(split_kernel, split_ms, bf16_peak, note16) \
             if split_ms else None
     else:
-        roofline = roof("square_split_kernel (tcgen05)", split_ms, bf16_peak, note16)
+        roofline = roof(split_kernel, split_ms, bf16_peak, note16)
         secondary = roof(k64, fp64_ms, p64, n64, b64) if fp64_ms else None
     if secondary is not None:
         roofline["secondary"] = secondary

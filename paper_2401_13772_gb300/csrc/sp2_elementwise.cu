@@ -42,8 +42,103 @@ __global__ void init_kernel(State* st, SolveParams p) {
   }
 }
 
-// One warp per row: R_i = sum_{j != i} |H_ij|; per-block min(H_ii - R_i) and
-// max(H_ii + R_i), then the last block combines the block results.
+// Exact sums of |x| over doubles with integer arithmetic only (GB300 issues
+// FP64 adds at a small fraction of its integer rate, and one add per entry
+// bounded the plain FP64 row sum at 0.18 of HBM). A 128-bit unsigned
+// fixed-point accumulator counts units of 2^(E - 1133), E the largest biased
+// exponent added so far: an entry |x| = m 2^(e - 1075) with a 53-bit m is m
+// shifted left by e - E + 58 <= 58 bits, below 2^111, so 2^16 entries fit.
+// When a larger exponent arrives the accumulator is shifted right to the new
+// unit, dropping bits 2^-58 below the new largest entry. The sum is rounded to
+// double once at the end: it is more accurate than a sum of FP64 adds.
+struct AbsSum {
+  unsigned long long lo, hi;  // the 128-bit value
+  int E;                      // biased exponent of the unit (0: nothing added yet)
+  int special;                // an infinity or NaN was added
+};
+
+__device__ __forceinline__ void abs_sum_shift(AbsSum& a, int d) {  // a >>= d, d >= 0
+  if (d <= 0) return;
+  if (d >= 128) {
+    a.lo = 0ull;
+    a.hi = 0ull;
+  } else if (d >= 64) {
+    a.lo = a.hi >> (d - 64);
+    a.hi = 0ull;
+  } else {
+    a.lo = (a.lo >> d) | (a.hi << (64 - d));
+    a.hi >>= d;
+  }
+}
+
+__device__ __forceinline__ void abs_sum_add(AbsSum& a, double x) {
+  const unsigned long long u =
+      (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  if (u == 0ull) return;
+  int e = (int)(u >> 52);
+  if (e == 0x7ff) {
+    a.special = 1;
+    return;
+  }
+  unsigned long long m = u & 0xfffffffffffffull;
+  if (e == 0) {
+    e = 1;  // subnormal: m 2^(1 - 1075)
+  } else {
+    m |= 1ull << 52;
+  }
+  if (e > a.E) {
+    abs_sum_shift(a, a.E == 0 ? 128 : e - a.E);
+    a.E = e;
+  }
+  const int sh = e - a.E + 58;
+  unsigned long long vl, vh = 0ull;
+  if (sh >= 0) {
+    vl = m << sh;
+    if (sh > 0) vh = m >> (64 - sh);
+  } else {
+    vl = sh > -64 ? (m >> -sh) : 0ull;
+  }
+  a.lo += vl;
+  a.hi += vh + (a.lo < vl ? 1ull : 0ull);
+}
+
+__device__ __forceinline__ void abs_sum_merge(AbsSum& a, AbsSum b) {
+  if (b.E > a.E) {
+    abs_sum_shift(a, a.E == 0 ? 128 : b.E - a.E);
+    a.E = b.E;
+  } else {
+    abs_sum_shift(b, b.E == 0 ? 128 : a.E - b.E);
+  }
+  a.lo += b.lo;
+  a.hi += b.hi + (a.lo < b.lo ? 1ull : 0ull);
+  a.special |= b.special;
+}
+
+__device__ __forceinline__ AbsSum abs_sum_warp(AbsSum a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    AbsSum b;
+    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    b.E = __shfl_xor_sync(0xffffffffu, a.E, o);
+    b.special = __shfl_xor_sync(0xffffffffu, a.special, o);
+    abs_sum_merge(a, b);
+  }
+  return a;
+}
+
+__device__ __forceinline__ double abs_sum_value(const AbsSum& a) {
+  // an infinite or NaN entry: an infinite radius, so the bounds are not finite
+  // and the solve reports EBOUNDS
+  if (a.special) return INFINITY;
+  if (a.E == 0) return 0.0;
+  const double v = __ull2double_rn(a.hi) * 18446744073709551616.0 + __ull2double_rn(a.lo);
+  return ldexp(v, a.E - 1133);
+}
+
+// One warp per row: R_i = sum_{j != i} |H_ij| (exact fixed-point sums, above);
+// per-block min(H_ii - R_i) and max(H_ii + R_i), then the last block combines
+// the block results.
 __global__ void __launch_bounds__(kEwThreads) gershgorin_kernel(const double* __restrict__ H,
                                                                 int64_t n, State* st,
                                                                 double* __restrict__ blk,
@@ -56,18 +151,18 @@ __global__ void __launch_bounds__(kEwThreads) gershgorin_kernel(const double* __
   double lo = INFINITY, hi = -INFINITY;
   for (int64_t i = (int64_t)blockIdx.x * (kEwThreads / 32) + wid; i < n; i += warps) {
     const double* row = H + i * n;
-    // four independent partial sums per lane keep four loads in flight
-    double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+    AbsSum acc{0ull, 0ull, 0, 0};
     int64_t j = lane;
-    for (; j + 96 < n; j += 128) {
-      r0 += (j == i) ? 0.0 : fabs(row[j]);
-      r1 += (j + 32 == i) ? 0.0 : fabs(row[j + 32]);
-      r2 += (j + 64 == i) ? 0.0 : fabs(row[j + 64]);
-      r3 += (j + 96 == i) ? 0.0 : fabs(row[j + 96]);
+    for (; j + 96 < n; j += 128) {  // four loads in flight per lane
+      const double v0 = __ldcs(row + j), v1 = __ldcs(row + j + 32);
+      const double v2 = __ldcs(row + j + 64), v3 = __ldcs(row + j + 96);
+      abs_sum_add(acc, j == i ? 0.0 : v0);
+      abs_sum_add(acc, j + 32 == i ? 0.0 : v1);
+      abs_sum_add(acc, j + 64 == i ? 0.0 : v2);
+      abs_sum_add(acc, j + 96 == i ? 0.0 : v3);
     }
-    for (; j < n; j += 32) r0 += (j == i) ? 0.0 : fabs(row[j]);
-    double r = (r0 + r1) + (r2 + r3);
-    r = warp_sum(r);
+    for (; j < n; j += 32) abs_sum_add(acc, j == i ? 0.0 : __ldcs(row + j));
+    const double r = abs_sum_value(abs_sum_warp(acc));
     const double d = row[i];
     lo = fmin(lo, d - r);
     hi = fmax(hi, d + r);

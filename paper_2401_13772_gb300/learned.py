@@ -280,9 +280,13 @@ def branch_labels(pred, batch, nocc, lab, margin, tol=1e-10):
     return targets(Y, kmax, bits=run["bits"], iters=run["iters"], reject=run["fallback"])
 
 
-def solve_learned(pred, batch, nocc, gersh, margin, judge_delta, tau=2.0, tol=1e-10):
-    """Batched solve with predicted bounds and the confident prefix of the
-    predicted branch sequence, judged by the trace rule."""
+def solve_learned(pred, batch, nocc, gersh, margin, judge_delta, tau=None, tol=1e-10):
+    """Batched solve with predicted bounds, judged by the trace rule. With tau
+    (e.g. 2.0) the confident prefix of the predicted branch sequence (leading
+    logits with |logit| >= tau) is predicted as well; the default predicts the
+    bounds only, which measured faster (predicted branches gain nothing once
+    the loop runs on the device without host syncs, and their rejections cost
+    products)."""
     Y = pred.predict(features(batch))
     bounds, bits, plen = solve_inputs(Y, gersh, margin, logit_tau=tau)
     out = batched_solve(batch, nocc, tol, bounds=bounds, pred_bits=bits, pred_len=plen,

@@ -42,6 +42,35 @@ def test_gershgorin_matches_oracle(pkg):
         assert abs(b[1] - emax) <= 1e-12 * max(1.0, abs(emax))
 
 
+def test_gershgorin_row_sums_are_exactly_rounded(pkg):
+    # the row sums R_i = sum_{j != i} |H_ij| are accumulated exactly (fixed point)
+    # and rounded once: against exact rational arithmetic on entries spread over
+    # 60 orders of magnitude, with zeros and subnormal entries
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    for n in (1, 7, 64, 333):
+        A = rng.standard_normal((n, n)) * np.exp(rng.uniform(-70, 70, (n, n)))
+        A[rng.uniform(size=(n, n)) < 0.3] = 0.0
+        if n > 1:
+            A[0, 1] = 5e-320  # subnormal
+        H = np.triu(A) + np.triu(A, 1).T
+        b = host(pkg.gershgorin_bounds(dev(H)))
+        lo = hi = None
+        for i in range(n):
+            R = sum((Fraction(abs(float(H[i, j]))) for j in range(n) if j != i), Fraction(0))
+            d = Fraction(float(H[i, i]))
+            lo = d - R if lo is None else min(lo, d - R)
+            hi = d + R if hi is None else max(hi, d + R)
+        scale = max(abs(float(lo)), abs(float(hi)), 1e-300)
+        assert abs(b[0] - float(lo)) <= 4e-16 * scale, (n, b[0], float(lo))
+        assert abs(b[1] - float(hi)) <= 4e-16 * scale, (n, b[1], float(hi))
+    # a non-finite entry gives non-finite bounds (the solve then reports EBOUNDS)
+    H = cube_hamiltonian(16, 1)[0]
+    H[3, 5] = H[5, 3] = np.inf
+    b = host(pkg.gershgorin_bounds(dev(H)))
+    assert not np.isfinite(b).all()
+
+
 def test_chain_512_matches_projector_and_golden_bits(pkg):
     H, nocc = chain_hamiltonian(512, -1.0, -0.6)
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "chain512_sp2.json")))

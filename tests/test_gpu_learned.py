@@ -195,7 +195,7 @@ def test_trained_predictor_saves_iterations(L):
     gersh = plain["bounds"]
     Y = P.predict(L.features(ev))
     rb = L.batched_solve(ev, nocc, bounds=L.predicted_bounds(Y, gersh, margin))
-    lr = L.solve_learned(P, ev, nocc, gersh, margin, judge_delta=0.5)
+    lr = L.solve_learned(P, ev, nocc, gersh, margin, judge_delta=0.5, tau=2.0)
     pp = plain["products"].double().mean().item()
     pb = rb["products"].double().mean().item()
     pl = lr["products"].double().mean().item()
