@@ -50,7 +50,10 @@ SPLIT_KERNEL = "square_split_persist_kernel (tcgen05, FP16x2)"
 NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200,
                ("square_df64_kernel (double-float, FP32 pipe)", 4096): 521512448,
                ("square_split_kernel (tcgen05)", 4096): 155314688,
-               (OZ_KERNEL, 4096): 658146304}
+               (SPLIT_KERNEL, 4096): 143759360,
+               (SPLIT_KERNEL, 8192): 1897807872,
+               (OZ_KERNEL, 4096): 674030080,
+               (OZ_KERNEL, 8192): 4488704000}
 NOMINAL_FP64_TFLOPS = 1.25
 # FP64 ceiling of this GPU: cuBLAS DGEMM 8192^3 (torch.matmul, float64) measured
 # on GB300 at 1.10 TFLOP/s (best of 5, CUDA events); used for the FP64 roofline

@@ -152,16 +152,40 @@ __global__ void __launch_bounds__(kEwThreads) gershgorin_kernel(const double* __
   for (int64_t i = (int64_t)blockIdx.x * (kEwThreads / 32) + wid; i < n; i += warps) {
     const double* row = H + i * n;
     AbsSum acc{0ull, 0ull, 0, 0};
-    int64_t j = lane;
-    for (; j + 96 < n; j += 128) {  // four loads in flight per lane
-      const double v0 = __ldcs(row + j), v1 = __ldcs(row + j + 32);
-      const double v2 = __ldcs(row + j + 64), v3 = __ldcs(row + j + 96);
-      abs_sum_add(acc, j == i ? 0.0 : v0);
-      abs_sum_add(acc, j + 32 == i ? 0.0 : v1);
-      abs_sum_add(acc, j + 64 == i ? 0.0 : v2);
-      abs_sum_add(acc, j + 96 == i ? 0.0 : v3);
+    int64_t j = 0;
+    if ((n & 1) == 0 && (reinterpret_cast<uintptr_t>(H) & 15u) == 0) {
+      // rows start on 16 bytes: pairs of entries, four 16-byte loads in flight
+      // per lane (eight entries)
+      const double2* row2 = reinterpret_cast<const double2*>(row);
+      const int64_t np = n >> 1;
+      int64_t q = lane;
+      for (; q + 96 < np; q += 128) {
+        double2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldcs(row2 + q + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t jj = 2 * (q + 32 * u);
+          abs_sum_add(acc, jj == i ? 0.0 : v[u].x);
+          abs_sum_add(acc, jj + 1 == i ? 0.0 : v[u].y);
+        }
+      }
+      for (; q < np; q += 32) {
+        const double2 v = __ldcs(row2 + q);
+        abs_sum_add(acc, 2 * q == i ? 0.0 : v.x);
+        abs_sum_add(acc, 2 * q + 1 == i ? 0.0 : v.y);
+      }
+    } else {
+      for (j = lane; j + 96 < n; j += 128) {  // four loads in flight per lane
+        const double v0 = __ldcs(row + j), v1 = __ldcs(row + j + 32);
+        const double v2 = __ldcs(row + j + 64), v3 = __ldcs(row + j + 96);
+        abs_sum_add(acc, j == i ? 0.0 : v0);
+        abs_sum_add(acc, j + 32 == i ? 0.0 : v1);
+        abs_sum_add(acc, j + 64 == i ? 0.0 : v2);
+        abs_sum_add(acc, j + 96 == i ? 0.0 : v3);
+      }
+      for (; j < n; j += 32) abs_sum_add(acc, j == i ? 0.0 : __ldcs(row + j));
     }
-    for (; j < n; j += 32) abs_sum_add(acc, j == i ? 0.0 : __ldcs(row + j));
     const double r = abs_sum_value(abs_sum_warp(acc));
     const double d = row[i];
     lo = fmin(lo, d - r);
@@ -373,30 +397,60 @@ __global__ void __launch_bounds__(kEwThreads) x0_df_kernel(const double* __restr
   ih = (float)inv_w;
   il = (float)(inv_w - (double)ih);
   float trh = 0.0f, trl = 0.0f, frh = 0.0f, frl = 0.0f;
+  // X0 entry (r, c) from h (inside the n x n block) as a double-float pair
+  auto entry = [&](int64_t r, int64_t c, double h, float& xh, float& xl) {
+    float hh, hl;
+    split_df(h, hh, hl);
+    if (r == c) {  // emax - h
+      float s, t;
+      two_sum_f(eh, -hh, s, t);
+      t += el - hl;
+      fast_two_sum_f(s, t, hh, hl);
+      df_mul(hh, hl, ih, il, xh, xl);
+      df_acc(trh, trl, xh, xl);
+    } else {
+      df_mul(-hh, -hl, ih, il, xh, xl);
+    }
+    // x^2 in double-float (xl^2 is below the pair's precision)
+    const float p = xh * xh;
+    const float e = fmaf(xh, xh, -p) + 2.0f * xh * xl;
+    df_acc(frh, frl, p, e);
+  };
+  // four consecutive entries per thread and step: two 16-byte loads of H (rows
+  // start on 16 bytes when n is even) and one 16-byte store per plane
+  const bool vec = (n & 1) == 0 && (reinterpret_cast<uintptr_t>(H) & 15u) == 0;
   for (int64_t r = blockIdx.x; r < ld; r += gridDim.x) {
-    for (int64_t c = threadIdx.x; c < ld; c += kEwThreads) {
-      const size_t idx = (size_t)r * ld + c;
-      float xh = 0.0f, xl = 0.0f;
-      if (r < n && c < n) {
-        float hh, hl;
-        split_df(H[r * n + c], hh, hl);
-        if (r == c) {  // emax - h
-          float s, t;
-          two_sum_f(eh, -hh, s, t);
-          t += el - hl;
-          fast_two_sum_f(s, t, hh, hl);
-          df_mul(hh, hl, ih, il, xh, xl);
-          df_acc(trh, trl, xh, xl);
-        } else {
-          df_mul(-hh, -hl, ih, il, xh, xl);
+    const double* Hr = H + r * n;
+#pragma unroll 2
+    for (int64_t c = 4 * threadIdx.x; c < ld; c += 4 * kEwThreads) {
+      double h[4];
+      bool in[4];
+      if (vec && r < n && c + 3 < n) {
+        const double2 a = __ldcs(reinterpret_cast<const double2*>(Hr + c));
+        const double2 b = __ldcs(reinterpret_cast<const double2*>(Hr + c + 2));
+        h[0] = a.x;
+        h[1] = a.y;
+        h[2] = b.x;
+        h[3] = b.y;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) in[e] = true;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          in[e] = r < n && c + e < n;
+          h[e] = in[e] ? Hr[c + e] : 0.0;
         }
-        // x^2 in double-float (xl^2 is below the pair's precision)
-        const float p = xh * xh;
-        const float e = fmaf(xh, xh, -p) + 2.0f * xh * xl;
-        df_acc(frh, frl, p, e);
       }
-      Xf[idx] = xh;
-      Xf[plane + idx] = xl;
+      float xh[4], xl[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        xh[e] = 0.0f;
+        xl[e] = 0.0f;
+        if (in[e]) entry(r, c + e, h[e], xh[e], xl[e]);
+      }
+      const size_t idx = (size_t)r * ld + c;
+      *reinterpret_cast<float4*>(Xf + idx) = make_float4(xh[0], xh[1], xh[2], xh[3]);
+      *reinterpret_cast<float4*>(Xf + plane + idx) = make_float4(xl[0], xl[1], xl[2], xl[3]);
     }
   }
   double tr = (double)trh + (double)trl, fr = (double)frh + (double)frl;

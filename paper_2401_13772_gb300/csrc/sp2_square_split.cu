@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int T = ld / BM;
   int I, J;
-  tri_tile(blockIdx.x, T, I, J);
+  band_tile<8>(blockIdx.x, T, I, J);  // tiles running together share few operand panels
   const int row_a = I * BM, row_b = J * BN;
 
   // shared memory: stage ring (1024-aligned), then barriers

@@ -71,6 +71,32 @@ def test_gershgorin_row_sums_are_exactly_rounded(pkg):
     assert not np.isfinite(b).all()
 
 
+@pytest.mark.parametrize("n", [301, 300])
+def test_odd_order_and_unaligned_input(pkg, n):
+    # an odd order (rows not on 16-byte boundaries) and an H whose first entry
+    # sits 8 bytes past a 16-byte boundary: the O(n^2) kernels take their
+    # scalar paths; bounds and solves must not change
+    import torch
+    rng = np.random.default_rng(n)
+    nocc = n // 2
+    w = np.concatenate([rng.uniform(-3.0, -0.5, nocc), rng.uniform(0.5, 3.0, n - nocc)])
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    H = (Q * w) @ Q.T
+    H = (H + H.T) / 2
+    Dref = Q[:, :nocc] @ Q[:, :nocc].T
+    buf = torch.zeros(n * n + 1, dtype=torch.float64, device="cuda:0")
+    Hv = buf[1:].view(n, n)
+    Hv.copy_(torch.from_numpy(H))
+    assert Hv.data_ptr() % 16 == 8
+    b = host(pkg.gershgorin_bounds(Hv))
+    emin, emax = oracle.gershgorin_bounds(H)
+    assert abs(b[0] - emin) <= 1e-12 * abs(emin) and abs(b[1] - emax) <= 1e-12 * abs(emax)
+    D, info = pkg.sp2_dense_ex(Hv, nocc, 1e-12)
+    assert info["status"] == "OK" and np.abs(host(D) - Dref).max() <= TOL_FP64
+    D, info = pkg.sp2_dense_ex(Hv, nocc, 1e-10, prec="mixed_fp16", fp64_prefix=8)
+    assert info["status"] == "OK" and np.abs(host(D) - Dref).max() <= 1e-5
+
+
 def test_chain_512_matches_projector_and_golden_bits(pkg):
     H, nocc = chain_hamiltonian(512, -1.0, -0.6)
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "chain512_sp2.json")))
