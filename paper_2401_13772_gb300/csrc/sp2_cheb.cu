@@ -416,7 +416,9 @@ struct SumTable {
 };
 
 template <int F, int KB, int MB, int EPT>
-__global__ void __launch_bounds__(EW_THREADS)
+// the 16 x 16 table runs three CTAs per SM (at most 85 registers): this pass is
+// bound by memory, and one CTA per SM kept too few loads in flight
+__global__ void __launch_bounds__(EW_THREADS, KB == 16 ? 3 : 1)
     cheb_sum_fast_kernel(Pool pool, int ld, int k, int m,
                          const __grid_constant__ SumTable<KB, MB> tab, double* __restrict__ D,
                          int64_t n, const int* __restrict__ gerr) {
