@@ -114,6 +114,14 @@ typedef struct {
                            barrier that nothing arrives on, so the solve must end with
                            PROGRESS_ETIMEOUT after wait_limit_us. Needs a mode with
                            tensor-core products (not FP64 or DF64), else PROGRESS_EINVAL */
+  int32_t split_tile;   /* tile of the dense FP16 split products (FP32_SPLIT, MIXED_FP16):
+                           0 (default) or 1 = 128 x 128 tiles; 2 = 128 x 256 tiles (one
+                           tensor-core product of N = 256, so the 128-row operand is read
+                           once per 256 columns; slower on GB300: 1.26 against 1.13 ms
+                           per product at n = 8192). Both issue the same products per
+                           element in the same order: D is the same bit for bit. Other
+                           values: PROGRESS_EINVAL; ignored by the other modes */
+  int32_t reserved0;    /* set to 0 */
 } progress_opts_t;
 
 /* Result of one solve, read back from the device by the calls that take it. */

@@ -28,7 +28,8 @@ class Opts(ctypes.Structure):
                 ("loop_mode", ctypes.c_int32), ("slice_fixed", ctypes.c_int32),
                 ("loop_events", ctypes.c_void_p * 2), ("fp64_impl", ctypes.c_int32),
                 ("tau", ctypes.c_float), ("wait_limit_us", ctypes.c_int32),
-                ("stall_test", ctypes.c_int32)]
+                ("stall_test", ctypes.c_int32), ("split_tile", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

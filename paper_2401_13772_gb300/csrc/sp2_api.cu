@@ -52,7 +52,7 @@ struct Workspace {
   // cached loop graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int g_ld = -1, g_prec = -1, g_fmt = -1, g_df = -1, g_oz = -1;
+  int g_ld = -1, g_prec = -1, g_fmt = -1, g_df = -1, g_oz = -1, g_tile = -1;
   float g_tau = -1.0f;
 };
 
@@ -64,7 +64,7 @@ void free_graph(Workspace* w) {
   if (w->graph) cudaGraphDestroy(w->graph);
   w->exec = nullptr;
   w->graph = nullptr;
-  w->g_ld = w->g_prec = w->g_fmt = w->g_df = w->g_oz = -1;
+  w->g_ld = w->g_prec = w->g_fmt = w->g_df = w->g_oz = w->g_tile = -1;
   w->g_tau = -1.0f;
 }
 
@@ -214,7 +214,7 @@ progress_status_t queue_steps(Workspace* w, const sp2::SolveParams& p, unsigned 
 
 progress_status_t build_graph(Workspace* w, const sp2::SolveParams& p) {
   if (w->exec && w->g_ld == p.ld && w->g_prec == p.prec && w->g_fmt == p.slice_fmt &&
-      w->g_df == p.df64 && w->g_oz == p.oz && w->g_tau == p.tau)
+      w->g_df == p.df64 && w->g_oz == p.oz && w->g_tau == p.tau && w->g_tile == p.split_tile)
     return PROGRESS_OK;
   free_graph(w);
   cudaGraph_t g = nullptr;
@@ -264,6 +264,7 @@ progress_status_t build_graph(Workspace* w, const sp2::SolveParams& p) {
   w->g_df = p.df64;
   w->g_oz = p.oz;
   w->g_tau = p.tau;
+  w->g_tile = p.split_tile;
   return PROGRESS_OK;
 }
 
@@ -384,6 +385,7 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   if (!(o.tau >= 0.0f) || !isfinite(o.tau)) return fail(PROGRESS_EINVAL, "tau must be finite and >= 0");
   if (o.wait_limit_us < 0) return fail(PROGRESS_EINVAL, "wait_limit_us must be >= 0");
   if (o.stall_test != 0 && o.stall_test != 1) return fail(PROGRESS_EINVAL, "stall_test must be 0 or 1");
+  if (o.split_tile < 0 || o.split_tile > 2) return fail(PROGRESS_EINVAL, "split_tile must be 0, 1 or 2");
   if (o.stall_test && (o.prec == PROGRESS_FP64 || o.prec == PROGRESS_DF64))
     return fail(PROGRESS_EINVAL, "stall_test needs a mode with tensor-core products");
   if (o.tau > 0.0f && (o.prec != PROGRESS_FP32_SPLIT || o.slice_fixed))
@@ -441,6 +443,7 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   p.wait_ns = o.wait_limit_us > 0 ? 1000ull * (unsigned long long)o.wait_limit_us
                                   : 2000000000ull;
   p.stall_test = o.stall_test;
+  p.split_tile = o.split_tile;
   // round-off floor of the refinement: 2 n u with u the absolute accuracy of
   // one FP64-accurate product entry (digit products ~2^-40, double-float
   // ~2^-44, native FP64 ~2^-52; entries of X are at most 1)

@@ -41,6 +41,7 @@ struct SolveParams {
   unsigned long long wait_ns;  // bound on each pipeline wait of the tensor-core kernels
   int stall_test;              // test of the bounded waits (see progress_opts_t)
   double floor_acc;            // MIXED: round-off floor of the refinement's idempotency
+  int split_tile;              // FP16x2 split product: 0 / 1 = 128 x 128 tiles, 2 = 128 x 256
 };
 
 cudaError_t launch_init(const DevBuffers& b, const SolveParams& p, cudaStream_t s);
@@ -68,6 +69,10 @@ int oz_max_order();
 cudaError_t launch_square_split(const DevBuffers& b, const SolveParams& p,
                                 unsigned long long cond_handle, cudaStream_t s);
 bool split_tensor_maps_ready(const DevBuffers& b, int ld, int fmt);
+// The FP16x2 split product on 128 x 256 tiles (one tcgen05.mma of N = 256 per
+// product group); launch_square_split calls it when split_tile is 2.
+cudaError_t launch_square_wide(const DevBuffers& b, const SolveParams& p,
+                               unsigned long long cond_handle, cudaStream_t s);
 // Thresholded SP2: tile flags of X0 into tflags[0] (a tile of H with a
 // non-zero, or a diagonal tile) and "unknown content" into tflags[1].
 cudaError_t launch_tile_flags(const double* H, int64_t n, int ld, const DevBuffers& b,

@@ -1314,6 +1314,7 @@ cudaError_t launch_square_split(const DevBuffers& b, const SolveParams& p,
     }
     return cudaGetLastError();
   }
+  if (!fmt_bf16(p.slice_fmt) && p.split_tile == 2) return launch_square_wide(b, p, cond_handle, s);
   if (!fmt_bf16(p.slice_fmt)) {
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);

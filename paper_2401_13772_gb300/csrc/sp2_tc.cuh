@@ -163,6 +163,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
+// 32 lanes x 8 columns of 32-bit values: this thread's lane, 8 columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+}
+
 // 32 lanes x 16 columns of 32-bit values from this thread's registers.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
   asm volatile(
@@ -171,6 +180,14 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
       "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
       "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
       "r"(r[15])
+      : "memory");
+}
+
+// 32 lanes x 8 columns of 32-bit values from this thread's registers.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
       : "memory");
 }
 
@@ -239,6 +256,45 @@ __device__ __forceinline__ void band_tile(int t, int T, int& I, int& J) {
     t -= count;
     b0 += g;
   }
+}
+
+// Wide tiles of a symmetric product: 128 rows (row block I, 0 <= I < T) by 256
+// columns (column pair P, 0 <= P < T2 = ceil(T / 2), columns 256 P .. 256 P + 255).
+// A tile is needed iff it reaches the diagonal or lies above it: P >= I / 2.
+// Order as band_tile: row blocks in bands of G (G even); a band walks P upward
+// from its first pair and takes the rows I <= 2 P + 1 of the band at each P.
+__host__ __device__ inline int wide_tile_count(int T) {
+  const int T2 = (T + 1) / 2, q = T / 2;
+  // sum over I of (T2 - floor(I / 2))
+  return T * T2 - (q * (q - 1) + ((T & 1) ? q : 0));
+}
+
+template <int G>
+__host__ __device__ inline void wide_tile(int t, int T, int& I, int& P) {
+  static_assert(G % 2 == 0, "bands start on an even row block");
+  const int T2 = (T + 1) / 2;
+  for (int b0 = 0; b0 < T; b0 += G) {
+    const int g = T - b0 < G ? T - b0 : G;  // rows in this band
+    int p = b0 / 2;
+    for (; p < T2; ++p) {  // head: pairs that hold fewer than g of the band's rows
+      const int rows = 2 * (p - b0 / 2) + 2;
+      if (rows >= g) break;
+      if (t < rows) {
+        I = b0 + t;
+        P = p;
+        return;
+      }
+      t -= rows;
+    }
+    const int body = g * (T2 - p);
+    if (t < body) {
+      P = p + t / g;
+      I = b0 + t % g;
+      return;
+    }
+    t -= body;
+  }
+  I = P = -1;  // t out of range
 }
 
 }  // namespace tc

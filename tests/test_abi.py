@@ -45,11 +45,13 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_sizes_match_header_layout():
     from paper_2401_13772_gb300 import _lib
-    # progress_opts_t: 4 int32, 2 double, 2 int32, 2 pointers, int32 reserved[4]
-    assert ctypes.sizeof(_lib.Opts) == 4 * 4 + 2 * 8 + 2 * 4 + 2 * 8 + 4 * 4
+    # progress_opts_t: 4 int32, 2 double, 2 int32, 2 pointers, then fp64_impl, tau,
+    # wait_limit_us, stall_test, split_tile, reserved0 (4 bytes each)
+    assert ctypes.sizeof(_lib.Opts) == 4 * 4 + 2 * 8 + 2 * 4 + 2 * 8 + 6 * 4
     assert _lib.Opts.emin.offset == 16 and _lib.Opts.loop_mode.offset == 32
     assert _lib.Opts.loop_events.offset == 40
     assert _lib.Opts.fp64_impl.offset == 56 and _lib.Opts.tau.offset == 60
+    assert _lib.Opts.split_tile.offset == 72
     # progress_info_t: 6 int32, 4 double, 4 uint64, uint64 kblocks
     assert ctypes.sizeof(_lib.Info) == 6 * 4 + 4 * 8 + 4 * 8 + 8
     assert _lib.Info.emin.offset == 24 and _lib.Info.bits.offset == 56

@@ -31,14 +31,19 @@ def pkg():
 
 
 @pytest.mark.parametrize("loop_mode", [0, 1])
-@pytest.mark.parametrize("prec,gate", [("fp32_split", 1e-4), ("mixed_fp16", 1e-5)])
-def test_wait_that_runs_out_reports_etimeout_then_solves_again(pkg, prec, gate, loop_mode):
+@pytest.mark.parametrize("prec,gate,split_tile", [("fp32_split", 1e-4, 2), ("fp32_split", 1e-4, 1),
+                                                  ("mixed_fp16", 1e-5, 0)])
+def test_wait_that_runs_out_reports_etimeout_then_solves_again(pkg, prec, gate, split_tile,
+                                                               loop_mode):
+    """FP32_SPLIT stalls in the split product (128 x 256 tiles for split_tile 2,
+    128 x 128 for 1, the default); MIXED_FP16 in the first digit product of its
+    prefix."""
     import torch
-    H, nocc = cube_hamiltonian(64, 7)  # n = 256: 3 product tiles
+    H, nocc = cube_hamiltonian(64, 7)  # n = 256: 3 (128 x 128) or 2 (128 x 256) tiles
     Hd = torch.from_numpy(H).to("cuda:0")
     w, V = oracle.jacobi_eigh(H)
     Dref, _ = oracle.density_projector(w, V, nocc)
-    opts = dict(prec=prec, fp64_prefix=8, loop_mode=loop_mode)
+    opts = dict(prec=prec, fp64_prefix=8, loop_mode=loop_mode, split_tile=split_tile)
     D, info = pkg.sp2_dense_ex(Hd, nocc, 1e-10, wait_limit_us=2000, stall_test=1,
                                raise_on_status=False, **opts)
     assert info["status"] == "ETIMEOUT", info

@@ -42,12 +42,14 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-@pytest.mark.parametrize("prec", ["fp32_split", "mixed_bf16"])
+@pytest.mark.parametrize("prec,split_tile", [("fp32_split", 2), ("fp32_split", 1),
+                                              ("mixed_bf16", 0)])
 @pytest.mark.parametrize("sites", [32, 75, 160])
-def test_single_split_product_matches_fp64(pkg, prec, sites):
-    # n = 128 (one tile), 300 (ragged, 3x3 tiles), 640 (5x5 tiles)
+def test_single_split_product_matches_fp64(pkg, prec, split_tile, sites):
+    # n = 128 (one tile), 300 (ragged, 3x3 tiles of 128 x 128, an odd number of
+    # 128-column blocks for the 128 x 256 tiles), 640 (5x5 tiles)
     H, nocc = cube_hamiltonian(sites, 21)
-    kw = {"prec": prec, "maxiter": 1}
+    kw = {"prec": prec, "maxiter": 1, "split_tile": split_tile}
     if prec.startswith("mixed"):
         kw["fp64_prefix"] = 0
     D, info = pkg.sp2_dense_ex(dev(H), nocc, 0.0, raise_on_status=False, **kw)
@@ -106,3 +108,33 @@ def test_split_degenerate_and_status(pkg):
     assert info["status"] == "EBOUNDS"
     D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-10, prec="mixed_bf16")
     assert info["converged"]
+
+
+@pytest.mark.parametrize("prec", ["fp32_split", "mixed_fp16"])
+@pytest.mark.parametrize("sites", [75, 250, 512, 700])
+def test_wide_and_square_tiles_agree_bit_for_bit(pkg, prec, sites):
+    """The FP16 split product on 128 x 256 tiles issues, per element, the same
+    tensor-core products in the same order as the 128 x 128 kernel (leading
+    group in 256-k chunks, corrections over the whole K), so whole solves give
+    the same D and the same branch sequence. n = 300, 1000, 2048, 2800: ld =
+    384, 1024, 2048, 2816, i.e. 3, 8, 16, 22 blocks of 128 (odd counts leave a
+    half-empty last column pair); the mixed solves also write FP64 X' from the
+    split epilogue before the refinement. Only the traces that each kernel sums
+    for the branch test may differ, in the order of their partial sums."""
+    H, nocc = cube_hamiltonian(sites, 33)
+    Hd = dev(H)
+    kw = dict(prec=prec, fp64_prefix=8)
+    Dw, iw = pkg.sp2_dense_ex(Hd, nocc, 1e-9, split_tile=2, **kw)
+    Ds, is_ = pkg.sp2_dense_ex(Hd, nocc, 1e-9, split_tile=1, **kw)
+    assert iw["bits"] == is_["bits"] and iw["phase_iters"] == is_["phase_iters"]
+    # the traces of the last product are partial sums in each kernel's own order
+    assert abs(iw["trace"] - is_["trace"]) <= 1e-9 * nocc
+    a, b = host(Dw), host(Ds)
+    assert np.isfinite(a).all()
+    assert np.array_equal(a, b), float(np.abs(a - b).max())
+
+
+def test_split_tile_option_is_checked(pkg):
+    H, nocc = cube_hamiltonian(32, 5)
+    with pytest.raises(pkg.ProgressError):
+        pkg.sp2_dense_ex(dev(H), nocc, 1e-9, prec="fp32_split", split_tile=3)
