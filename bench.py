@@ -52,8 +52,10 @@ NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200,
                ("square_split_kernel (tcgen05)", 4096): 155314688,
                (SPLIT_KERNEL, 4096): 143759360,
                (SPLIT_KERNEL, 8192): 1897807872,
-               (OZ_KERNEL, 4096): 674030080,
-               (OZ_KERNEL, 8192): 4488704000}
+               # mean over one mixed solve's 12 launches (8 prefix products of 13
+               # digit products, 4 refinement products of 15)
+               (OZ_KERNEL, 4096): 570465856,
+               (OZ_KERNEL, 8192): 4121248106}
 NOMINAL_FP64_TFLOPS = 1.25
 # FP64 ceiling of this GPU: cuBLAS DGEMM 8192^3 (torch.matmul, float64) measured
 # on GB300 at 1.10 TFLOP/s (best of 5, CUDA events); used for the FP64 roofline
@@ -63,7 +65,10 @@ MEASURED_DGEMM_TFLOPS = 1.10
 # on its round-off floor, about n times the slices' 2^-22 resolution)
 FP32_GATE = {"max_abs_err": 1e-4, "trace_err_per_n": 4.0 * 2.0 ** -22}
 DF_OPS = 12  # FP32 instructions per double-float multiply-add in square_df64_kernel
-OZ_PRODUCTS = 15  # BF16 digit products per FP64-accurate product in square_oz_kernel
+# BF16 digit products per FP64-accurate product in square_oz_kernel: all 15 in
+# the refinement, 13 in the prefix (the library's default short form)
+OZ_PRODUCTS = 15
+OZ_PRODUCTS_PREFIX = 13
 IMPL_DTYPE = {"double-float": "double-float", "native fp64": "f64",
               "digits": "bf16 digit products (f32 accumulate)"}
 
@@ -1120,9 +1125,13 @@ def main():
         k64, p64, n64, b64 = ("square_df64_kernel (double-float, FP32 pipe)", df_peak, notedf,
                               "alu")
     elif impl == "digits":
-        k64, p64, b64 = (OZ_KERNEL, bf16_peak / OZ_PRODUCTS, "tensor")
-        n64 = (f"fp16/bf16 dense, {peak_src} burst / {OZ_PRODUCTS} BF16 digit products per "
-               f"FP64-accurate product")
+        # mean digit products per FP64-accurate product of this solve
+        oz_mean = ((phases[0] * OZ_PRODUCTS_PREFIX + phases[2] * OZ_PRODUCTS) / n_fp64
+                   if n_fp64 else float(OZ_PRODUCTS))
+        k64, p64, b64 = (OZ_KERNEL, bf16_peak / oz_mean, "tensor")
+        n64 = (f"fp16/bf16 dense, {peak_src} burst / {oz_mean:.2f} BF16 digit products per "
+               f"FP64-accurate product ({phases[0]} prefix products of {OZ_PRODUCTS_PREFIX}, "
+               f"{phases[2]} refinement products of {OZ_PRODUCTS})")
     else:
         k64, p64, n64, b64 = ("square_fp64_kernel (FP64 DMMA)", fp64_peak, note64, "tensor")
     split_kernel = (SPLIT_KERNEL if "bf16" not in args.prec

@@ -121,7 +121,12 @@ typedef struct {
                            per product at n = 8192). Both issue the same products per
                            element in the same order: D is the same bit for bit. Other
                            values: PROGRESS_EINVAL; ignored by the other modes */
-  int32_t reserved0;    /* set to 0 */
+  int32_t prefix_full;  /* MIXED_* with digit products (fp64_impl 3, the default up to
+                           n = 8192): 0 (default) = the FP64-accurate prefix products take
+                           13 of the 15 digit products: x0 x4^T + x4 x0^T is dropped, at
+                           most 2 sqrt(n) 2^-36 per entry (random sign, ~1e-11), and digit
+                           4 is not loaded; the refinement always takes all 15 (~2^-40).
+                           1 = all 15 in the prefix too. Other values: PROGRESS_EINVAL */
 } progress_opts_t;
 
 /* Result of one solve, read back from the device by the calls that take it. */

@@ -66,7 +66,7 @@ def gershgorin_bounds(H, out=None, stream=None):
 
 def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None, emax=None,
               loop_mode=0, loop_events=None, slice_fixed=0, fp64_impl=0, tau=0.0,
-              wait_limit_us=0, stall_test=0, split_tile=0):
+              wait_limit_us=0, stall_test=0, split_tile=0, prefix_full=0):
     o = Opts()
     load().progress_opts_default(ctypes.byref(o))
     o.prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
@@ -82,6 +82,7 @@ def make_opts(prec="fp64", rule="nearer", fp64_prefix=12, maxiter=100, emin=None
     o.wait_limit_us = int(wait_limit_us)
     o.stall_test = int(stall_test)
     o.split_tile = int(split_tile)
+    o.prefix_full = int(prefix_full)
     if loop_events is not None:
         # torch.cuda.Event pair, already created (recorded once)
         o.loop_events[0] = loop_events[0].cuda_event
@@ -106,7 +107,7 @@ def sp2_dense(H, nocc, tol, D=None, stream=None):
 def sp2_dense_ex(H, nocc, tol, D=None, info=True, stream=None, raise_on_status=True, **opts):
     """SP2 solve with options (prec, rule, fp64_prefix, maxiter, emin, emax,
     loop_mode, loop_events, slice_fixed, fp64_impl, tau, wait_limit_us,
-    stall_test, split_tile). With info=True it synchronizes and returns (D, info dict)."""
+    stall_test, split_tile, prefix_full). With info=True it synchronizes and returns (D, info dict)."""
     import torch
     _check_matrix(H, "H")
     if D is None:

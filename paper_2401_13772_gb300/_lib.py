@@ -29,7 +29,7 @@ class Opts(ctypes.Structure):
                 ("loop_events", ctypes.c_void_p * 2), ("fp64_impl", ctypes.c_int32),
                 ("tau", ctypes.c_float), ("wait_limit_us", ctypes.c_int32),
                 ("stall_test", ctypes.c_int32), ("split_tile", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32)]
+                ("prefix_full", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

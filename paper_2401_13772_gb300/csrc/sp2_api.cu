@@ -386,6 +386,7 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
   if (o.wait_limit_us < 0) return fail(PROGRESS_EINVAL, "wait_limit_us must be >= 0");
   if (o.stall_test != 0 && o.stall_test != 1) return fail(PROGRESS_EINVAL, "stall_test must be 0 or 1");
   if (o.split_tile < 0 || o.split_tile > 2) return fail(PROGRESS_EINVAL, "split_tile must be 0, 1 or 2");
+  if (o.prefix_full != 0 && o.prefix_full != 1) return fail(PROGRESS_EINVAL, "prefix_full must be 0 or 1");
   if (o.stall_test && (o.prec == PROGRESS_FP64 || o.prec == PROGRESS_DF64))
     return fail(PROGRESS_EINVAL, "stall_test needs a mode with tensor-core products");
   if (o.tau > 0.0f && (o.prec != PROGRESS_FP32_SPLIT || o.slice_fixed))
@@ -444,6 +445,7 @@ progress_status_t progress_sp2_dense_ex(const double* dH, int64_t n, int64_t noc
                                   : 2000000000ull;
   p.stall_test = o.stall_test;
   p.split_tile = o.split_tile;
+  p.prefix_full = o.prefix_full;
   // round-off floor of the refinement: 2 n u with u the absolute accuracy of
   // one FP64-accurate product entry (digit products ~2^-40, double-float
   // ~2^-44, native FP64 ~2^-52; entries of X are at most 1)

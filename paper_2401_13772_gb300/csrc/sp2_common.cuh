@@ -63,6 +63,9 @@ struct State {
   unsigned long long wait_ns;  // bound on each pipeline wait of the tensor-core kernels
   int stall_test;              // 1: CTA 0 of a tensor-core product waits on a barrier that
                                // nothing arrives on (test of the bounded waits)
+  int prefix_full;             // MIXED, digit products: 1 = all 15 digit products in the
+                               // FP64-accurate prefix too; 0 = 13 there (no x0 x4 pair),
+                               // all 15 in the refinement
   unsigned long long bits[4];
   double idem_hist[kMaxHist];
   double margin_hist[kMaxHist];

@@ -38,6 +38,7 @@ __global__ void init_kernel(State* st, SolveParams p) {
     st->wait_ns = p.wait_ns;
     st->floor_acc = p.floor_acc;
     st->stall_test = p.stall_test;
+    st->prefix_full = p.prefix_full;
     st->phase = (p.prec == PROGRESS_FP32_SPLIT) ? kPhaseSplit : kPhaseFP64;
   }
 }

@@ -42,6 +42,7 @@ struct SolveParams {
   int stall_test;              // test of the bounded waits (see progress_opts_t)
   double floor_acc;            // MIXED: round-off floor of the refinement's idempotency
   int split_tile;              // FP16x2 split product: 0 / 1 = 128 x 128 tiles, 2 = 128 x 256
+  int prefix_full;             // digit products of the MIXED prefix: 1 = all 15, 0 = 13
 };
 
 cudaError_t launch_init(const DevBuffers& b, const SolveParams& p, cudaStream_t s);

@@ -33,6 +33,16 @@
 // g2 + T is then summed in double-float (Knuth's two-sum), X' = S or 2X - S,
 // and X' is written back as double-float planes.
 //
+// Short form (the products of the prefix before the split phase, unless the
+// caller asks for all 15): without x0 x4^T + x4 x0^T, 13 products, and digit
+// 4 is not loaded. Digit 4 is at most 2^-36 per entry, so by Cauchy-Schwarz
+// over a row pair (row norms of x0 <= 1 + ...) the dropped pair is at most
+// 2 sqrt(K) 2^-36 per entry (2.6e-9 at K = 8192), of random sign, ~1e-11 in
+// practice. The other products with digits 3 and 4 cannot go: the digits are
+// fixed-point, so for the typical entry (~0.01) digit 1 carries most of the
+// value (rms ~1e-3) and x1 x3^T alone is ~1e-9 per entry, as large as the
+// relative 2^-22 of the split products that follow.
+//
 // Roles (one CTA per 128 x 128 upper-triangle tile, 384 threads):
 //   warp 0 lane 0 : TMA producer; per stage (16 k) and operand one 128 x 64
 //                   box of the interleaved plane (digits 0..3 of the 16 k in
@@ -226,6 +236,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       (prec == PROGRESS_MIXED_FP16 || prec == PROGRESS_MIXED_BF16) && phase == kPhaseFP64 &&
       (k_iter + 1 >= st->fp64_prefix);
   const size_t plane = (size_t)ld * ld;
+  // prefix products (before the split phase) may take 13 of the 15 digit
+  // products: no x0 x4^T + x4 x0^T, digit 4 not loaded (see the header)
+  const bool low = phase == kPhaseFP64 && __ldcg(&st->prefix_full) == 0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int T = ld / BM;
@@ -266,7 +279,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int KB = ld / BK;
   const int NC = (KB + CHUNK_KB - 1) / CHUNK_KB;
-  const uint32_t stage_bytes = same ? (uint32_t)(ND * BOX_BYTES) : (uint32_t)STAGE_BYTES;
+  const int nd_loaded = low ? ND - 1 : ND;  // digit 4 is not loaded for the short form
+  const uint32_t stage_bytes = (uint32_t)((same ? 1 : 2) * nd_loaded * BOX_BYTES);
   int issued = 0;
   if (warp == 0) {
     if (lane == 0) {
@@ -278,10 +292,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         // stage: A interleaved | B interleaved | A digit 4 | B digit 4
         const uint32_t sa = base + s * STAGE_BYTES;
         tma_load_2d(sa, &maps.p0, kb * 64, row_a, full_bar(s));
-        tma_load_2d(sa + 2 * IBOX_BYTES, &maps.p4, kb * BK, row_a, full_bar(s));
+        if (!low) tma_load_2d(sa + 2 * IBOX_BYTES, &maps.p4, kb * BK, row_a, full_bar(s));
         if (!same) {
           tma_load_2d(sa + IBOX_BYTES, &maps.p0, kb * 64, row_b, full_bar(s));
-          tma_load_2d(sa + 2 * IBOX_BYTES + BOX_BYTES, &maps.p4, kb * BK, row_b, full_bar(s));
+          if (!low)
+            tma_load_2d(sa + 2 * IBOX_BYTES + BOX_BYTES, &maps.p4, kb * BK, row_b, full_bar(s));
         }
       }
     }
@@ -318,10 +333,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         mma_f16(g2, a[0], b[2], idesc, c_acc);
         mma_f16(g2, a[1], b[1], idesc, 1u);
         mma_f16(g2, a[2], b[0], idesc, 1u);
-        // T: small terms first
-        mma_f16(tt, a[0], b[4], idesc, c_acc);
-        mma_f16(tt, a[4], b[0], idesc, 1u);
-        mma_f16(tt, a[1], b[3], idesc, 1u);
+        // T: small terms first (the short form drops the x0 x4 pair)
+        if (!low) {
+          mma_f16(tt, a[0], b[4], idesc, c_acc);
+          mma_f16(tt, a[4], b[0], idesc, 1u);
+        }
+        mma_f16(tt, a[1], b[3], idesc, low ? c_acc : 1u);
         mma_f16(tt, a[3], b[1], idesc, 1u);
         mma_f16(tt, a[2], b[2], idesc, 1u);
         mma_f16(tt, a[0], b[3], idesc, 1u);

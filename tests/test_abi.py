@@ -46,7 +46,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes_match_header_layout():
     from paper_2401_13772_gb300 import _lib
     # progress_opts_t: 4 int32, 2 double, 2 int32, 2 pointers, then fp64_impl, tau,
-    # wait_limit_us, stall_test, split_tile, reserved0 (4 bytes each)
+    # wait_limit_us, stall_test, split_tile, prefix_full (4 bytes each)
     assert ctypes.sizeof(_lib.Opts) == 4 * 4 + 2 * 8 + 2 * 4 + 2 * 8 + 6 * 4
     assert _lib.Opts.emin.offset == 16 and _lib.Opts.loop_mode.offset == 32
     assert _lib.Opts.loop_events.offset == 40

@@ -240,30 +240,38 @@ def test_df64_products_match_plain_sp2(pkg):
         assert np.abs(host(D) - Dref).max() <= TOL_FP64
 
 
-def test_digit_products_match_plain_sp2(pkg):
+@pytest.mark.parametrize("prefix_full,tol", [(1, 1e-10), (0, 1e-9)])
+def test_digit_products_match_plain_sp2(pkg, prefix_full, tol):
     """FP64-accurate products as exact BF16 digit products on the tensor cores
     (fp64_impl 3): with a prefix longer than the run, every product is one of
-    them; the iterates track the FP64 oracle's (digits carry 2^-44 absolute,
-    the products ~2^-40)."""
+    them; the iterates track the FP64 oracle's. All 15 digit products
+    (prefix_full 1): digits carry 2^-44 absolute, the products ~2^-40, gate
+    1e-10. The prefix's short form (13 products) drops x0 x4^T + x4 x0^T, at
+    most 2 sqrt(K) 2^-36 per entry and product (5e-10 at K = 300), of random
+    sign (~1e-11 typical): gate 1e-9. A wrong digit product is off by 1e-6 or
+    more."""
     for sites, seed in ((75, 5), (32, 3)):  # n = 300 (ragged, 3 row blocks), 128 (one tile)
         H, nocc = cube_hamiltonian(sites, seed)
         for k in (1, 2, 6, 14):
             D, info = pkg.sp2_dense_ex(dev(H), nocc, 0.0, prec="mixed_fp16", fp64_impl=3,
-                                       fp64_prefix=60, maxiter=k, raise_on_status=False)
+                                       fp64_prefix=60, maxiter=k, raise_on_status=False,
+                                       prefix_full=prefix_full)
             ref = oracle.sp2_plain(H, nocc, 0.0, stop_after=k)
             assert info["iters"] == k and info["bits"] == ref["bits"]
-            assert np.abs(host(D) - ref["D"]).max() <= 1e-10, (sites, k)
+            assert np.abs(host(D) - ref["D"]).max() <= tol, (sites, k)
             assert abs(info["trace"] - ref["t1"][-1]) <= 1e-8
 
 
 def test_digit_product_mixed_solve_meets_mixed_gate(pkg):
     """n = 1000 (8 chunks of 128 k for the exact G2 drain): the whole mixed
-    solve with digit-product prefix and refinement."""
+    solve with digit-product prefix (short form, and all 15 products) and
+    refinement."""
     H, nocc = cube_hamiltonian(250, 4)
     w, V = oracle.jacobi_eigh(H)
     Dref, _ = oracle.density_projector(w, V, nocc)
-    for fmt in ("mixed_fp16", "mixed_bf16"):
-        D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-10, prec=fmt, fp64_impl=3, fp64_prefix=8)
+    for fmt, prefix_full in (("mixed_fp16", 0), ("mixed_bf16", 0), ("mixed_fp16", 1)):
+        D, info = pkg.sp2_dense_ex(dev(H), nocc, 1e-10, prec=fmt, fp64_impl=3, fp64_prefix=8,
+                                   prefix_full=prefix_full)
         assert info["status"] == "OK" and info["converged"], info
         Dn = host(D)
         assert np.abs(Dn - Dref).max() <= 1e-5
