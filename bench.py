@@ -47,6 +47,7 @@ OZ_KERNEL = ("square_oz_kernel (BF16 digit products, tcgen05; time includes digi
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands, keyed by (kernel, n); see profiles/.
 SPLIT_KERNEL = "square_split_persist_kernel (tcgen05, FP16x2)"
+WIDE_KERNEL = "square_wide_kernel (tcgen05, FP16x2, 128 x 256 tiles)"
 NCU_TRAFFIC = {("square_fp64_kernel (FP64 DMMA)", 4096): 1101459200,
                ("square_df64_kernel (double-float, FP32 pipe)", 4096): 521512448,
                ("square_split_kernel (tcgen05)", 4096): 155314688,
@@ -100,6 +101,8 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--fp64-prefix", type=int, default=8)
+    ap.add_argument("--split-tile", type=int, default=0, choices=[0, 1, 2],
+                    help="tile of the FP16 split products: 0/1 = 128 x 128, 2 = 128 x 256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16-leg", dest="bf16_leg", action="store_false",
                     help="mixed_fp16 runs: skip the same solve with bf16 hi+mid+lo splits")
@@ -1030,7 +1033,7 @@ def main():
         return evs
 
     opts = dict(prec=args.prec, fp64_prefix=args.fp64_prefix, loop_mode=args.loop_mode,
-                fp64_impl=args.fp64_impl)
+                fp64_impl=args.fp64_impl, split_tile=args.split_tile)
     # warm-up (builds the loop graph) and the iteration count
     info = None
     for _ in range(max(1, args.warmup)):
@@ -1134,8 +1137,8 @@ def main():
                f"{phases[2]} refinement products of {OZ_PRODUCTS})")
     else:
         k64, p64, n64, b64 = ("square_fp64_kernel (FP64 DMMA)", fp64_peak, note64, "tensor")
-    split_kernel = (SPLIT_KERNEL if "bf16" not in args.prec
-                    else "square_split_kernel (tcgen05, BF16x3)")
+    split_kernel = ("square_split_kernel (tcgen05, BF16x3)" if "bf16" in args.prec
+                    else WIDE_KERNEL if args.split_tile == 2 else SPLIT_KERNEL)
     split_ms = None
     if n_split > 0:
         if n_fp64 == 0:
@@ -1143,9 +1146,10 @@ def main():
         else:
             sp_s, sp_e = mk_events(1)[0], mk_events(1)[0]
             pkg.sp2_dense_ex(H, nocc, args.tol, D=D, prec="fp32_split", fp64_prefix=0,
-                             loop_mode=args.loop_mode)
+                             loop_mode=args.loop_mode, split_tile=args.split_tile)
             _, sinfo = pkg.sp2_dense_ex(H, nocc, args.tol, D=D, prec="fp32_split",
-                                        loop_events=(sp_s, sp_e), loop_mode=args.loop_mode)
+                                        loop_events=(sp_s, sp_e), loop_mode=args.loop_mode,
+                                        split_tile=args.split_tile)
             torch.cuda.synchronize()
             split_ms = sp_s.elapsed_time(sp_e) / max(sinfo["iters"], 1)
     fp64_ms = None
@@ -1175,6 +1179,7 @@ def main():
                        "prec": args.prec, "tol": args.tol, "rule": "nearer",
                        "fp64_prefix": args.fp64_prefix,
                        "fp64_accurate_products": impl,
+                       **({"split_tile": "128x256"} if args.split_tile == 2 else {}),
                        "parallelism": f"replicas x{world}",
                        "l2": "flushed before each step (256 MiB write, outside events)"},
             "iters": iters, "status": qinfo["status"], "phase_iters": qinfo["phase_iters"],

@@ -21,8 +21,10 @@
 //                        runs them on concurrent streams; here they share one
 //                        launch). Then the m - 1 nested products
 //                        P_j = S_j + T_k P_{j+1}; the last writes D in FP64.
-//   cheb_sum_fast_kernel every S_j in one pass over T_1..T_{k-1} (the sums
-//                        are independent, Eq. 9), coefficients in the constant bank
+//   cheb_sum_staged_kernel / cheb_sum_fast_kernel
+//                        every S_j in one pass over T_1..T_{k-1} (the sums are
+//                        independent, Eq. 9), coefficients in the constant bank; the
+//                        staged pass (k <= 16) brings the T inputs by 3D TMA boxes
 //
 // Every matrix is a polynomial in Ht, so all of them are symmetric and
 // commute: a product tile (I, J), I <= J, reads the row panels I of A and J
@@ -506,6 +508,142 @@ cudaError_t launch_sum_fast(const Pool& pool, int ld, int k, int m, const std::v
   return cudaGetLastError();
 }
 
+// The 16 x 16 pass with its T inputs staged through shared memory. Measured on
+// cheb_sum_fast_kernel at N = 4096: its 30 slice streams of 4-byte loads per
+// element ran at about 1.1 TB/s (the loads alone took as long as the whole pass,
+// 0.95 ms; the stores alone 0.29 ms). Here one 3D TMA box per slice brings
+// T_1 .. T_{k-1} of a 4 x 128 chunk (k - 1 planes of 1 KB each) in long
+// sequential requests, SG_STAGES chunks ahead, and the threads compute from
+// shared memory with the same arithmetic and the same stores as the fast pass.
+// Persistent: CTA b takes chunks b, b + grid, ...; every wait is bounded.
+constexpr int SG_ROWS = 4;
+constexpr int SG_COLS = 128;
+constexpr int SG_STAGES = 3;
+static_assert(SG_ROWS * SG_COLS == 2 * EW_THREADS, "two elements per thread");
+
+struct SumMaps {
+  CUtensorMap m[3];  // per slice: the slot stack, boxes of SG_COLS x SG_ROWS x (k - 1)
+};
+
+template <int F>
+__global__ void __launch_bounds__(EW_THREADS, 2)
+    cheb_sum_staged_kernel(const __grid_constant__ SumMaps maps, Pool pool, int ld, int k,
+                           int m, const __grid_constant__ SumTable<16, 16> tab,
+                           double* __restrict__ D, int64_t n, int* __restrict__ gerr) {
+  constexpr int NS = fmt_slices(F);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t s_full[SG_STAGES];
+  __shared__ int s_err;
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = *(volatile const int*)gerr;
+  __syncthreads();
+  if (s_skip) return;  // an earlier launch of this solve failed (uniform)
+
+  const int nz = k - 1;  // T_1 .. T_{k-1} sit in slots 0 .. k - 2
+  constexpr uint32_t kPlane = SG_ROWS * SG_COLS * 2;  // bytes of one z plane of one slice
+  const uint32_t stage_bytes = (uint32_t)(NS * nz) * kPlane;
+  const int cpr = ld / SG_COLS;  // chunks per band of SG_ROWS rows
+  const int chunks = (ld / SG_ROWS) * cpr;
+  const int my = (chunks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  auto full = [&](int q) { return smem_u32(&s_full[q]); };
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    for (int q = 0; q < SG_STAGES; ++q) mbar_init(full(q), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  __syncthreads();
+  volatile int* err = &s_err;
+  // thread 0: the loads of this CTA's chunk `it` into stage it % SG_STAGES
+  auto issue = [&](int it) {
+    const int g = (int)blockIdx.x + it * (int)gridDim.x;
+    const int r0 = (g / cpr) * SG_ROWS, c0 = (g % cpr) * SG_COLS;  // c0: 256 B multiple
+    const int q = it % SG_STAGES;
+    const uint32_t dst = base + (uint32_t)q * stage_bytes;
+    mbar_expect_tx(full(q), stage_bytes);
+#pragma unroll
+    for (int sl = 0; sl < NS; ++sl)
+      tma_load_3d(dst + (uint32_t)(sl * nz) * kPlane, &maps.m[sl], c0, r0, 0, full(q));
+  };
+  int issued = 0;
+  if (threadIdx.x == 0)
+    for (; issued < SG_STAGES && issued < my; ++issued) issue(issued);
+
+  const int row = threadIdx.x / (SG_COLS / 2), col = 2 * (threadIdx.x % (SG_COLS / 2));
+  int it = 0;
+  for (; it < my; ++it) {
+    const int q = it % SG_STAGES;
+    const bool fail = !mbar_wait(full(q), (uint32_t)(it / SG_STAGES) & 1u, err);
+    if (__syncthreads_or(fail)) break;  // uniform
+    const uint16_t* sb = reinterpret_cast<const uint16_t*>(
+        smem_raw + (base + (uint32_t)q * stage_bytes - smem_u32(smem_raw)));
+    const int g = (int)blockIdx.x + it * (int)gridDim.x;
+    const int64_t r = (int64_t)(g / cpr) * SG_ROWS + row;
+    const int64_t c = (int64_t)(g % cpr) * SG_COLS + col;
+    const size_t e = (size_t)r * ld + (size_t)c;
+    const size_t area = (size_t)ld * ld;
+    float t[2][16];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) t[u][0] = (r == c + u) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int i = 1; i < 16; ++i) {
+      t[0][i] = t[1][i] = 0.0f;
+      if (i < k) {
+        const int off = ((i - 1) * SG_ROWS + row) * SG_COLS + col;  // elements in a slice box
+        const int sls = nz * SG_ROWS * SG_COLS;                     // elements per slice box
+        const uint32_t h = *reinterpret_cast<const uint32_t*>(sb + off);
+        const uint32_t l = *reinterpret_cast<const uint32_t*>(sb + sls + off);
+        const uint32_t w =
+            fmt_bf16(F) ? *reinterpret_cast<const uint32_t*>(sb + 2 * sls + off) : 0u;
+        t[0][i] = join_value<F>((uint16_t)(h & 0xffffu), (uint16_t)(l & 0xffffu),
+                                (uint16_t)(w & 0xffffu));
+        t[1][i] = join_value<F>((uint16_t)(h >> 16), (uint16_t)(l >> 16), (uint16_t)(w >> 16));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j < m) {
+        float acc[2] = {0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) acc[u] += tab.d[i * 16 + j] * t[u][i];
+        }
+        if (m == 1) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (r < n && c + u < n) D[r * n + c + u] = (double)acc[u];
+        } else {
+          uint16_t x[2][3];
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            split_value_f<F>(acc[u] * tab.inv_s[j], x[u][0], x[u][1], x[u][2]);
+          const size_t o = (size_t)(k + j) * area + e;
+#pragma unroll
+          for (int sl = 0; sl < NS; ++sl)
+            *reinterpret_cast<uint32_t*>(pool.s[sl] + o) =
+                (uint32_t)x[0][sl] | ((uint32_t)x[1][sl] << 16);
+        }
+      }
+    }
+    __syncthreads();  // every thread has read stage q: it may be refilled
+    if (threadIdx.x == 0 && issued < my) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(issued++);
+    }
+  }
+  if (*err) {
+    // failure path: let the copies still in flight land before the CTA exits
+    if (threadIdx.x == 0) {
+      for (int g = it; g < issued; ++g)
+        mbar_wait(full(g % SG_STAGES), (uint32_t)(g / SG_STAGES) & 1u, err, false,
+                  kWaitLimitNs / 10);
+      atomicExch(gerr, (int)PROGRESS_ETIMEOUT);
+    }
+  }
+}
+
 __global__ void cheb_trace_kernel(const double* __restrict__ D, int64_t n, double* out) {
   __shared__ double s[EW_THREADS / 32];
   double v = 0.0;
@@ -638,6 +776,49 @@ bool encode_stack(const Pool& pool, int ns, int ld, int nslots, bool bf16, Maps*
     if (r != CUDA_SUCCESS) return false;
   }
   return true;
+}
+
+// The staged 16 x 16 sum pass (2 <= k <= 16, m <= 16): maps of boxes
+// SG_COLS x SG_ROWS x (k - 1) over each slice's slot stack.
+template <int F>
+cudaError_t launch_sum_staged(const Pool& pool, int ld, int nslots, int k, int m,
+                              const std::vector<float>& d, const std::vector<float>& inv_s,
+                              double* D, int64_t n, int* err, cudaStream_t s) {
+  constexpr int NS = fmt_slices(F);
+  if (k < 2 || k > 16 || m > 16 || ld % SG_COLS || nslots < k - 1) return cudaErrorInvalidValue;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+  if (!enc) return cudaErrorInvalidValue;
+  SumMaps maps;
+  memset(&maps, 0, sizeof maps);
+  for (int j = 0; j < NS; ++j) {
+    cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)ld, (cuuint64_t)nslots};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * (cuuint64_t)ld * 2};
+    cuuint32_t box[3] = {(cuuint32_t)SG_COLS, (cuuint32_t)SG_ROWS, (cuuint32_t)(k - 1)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&maps.m[j], fmt_bf16(F) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+            3, (void*)pool.s[j], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  SumTable<16, 16> tab;
+  memset(&tab, 0, sizeof tab);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < m; ++j) tab.d[i * 16 + j] = d[(size_t)i * m + j];
+  for (int j = 0; j < m; ++j) tab.inv_s[j] = inv_s[j];
+  const int smem = 1024 + SG_STAGES * NS * (k - 1) * SG_ROWS * SG_COLS * 2;
+  cudaError_t e = cudaFuncSetAttribute(cheb_sum_staged_kernel<F>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  const int chunks = (ld / SG_ROWS) * (ld / SG_COLS);
+  const int grid = std::min(2 * nsm, chunks);
+  cheb_sum_staged_kernel<F><<<grid, EW_THREADS, smem, s>>>(maps, pool, ld, k, m, tab, D, n, err);
+  return cudaGetLastError();
 }
 
 template <int F>
@@ -835,7 +1016,9 @@ progress_status_t run(const double* dH, int64_t n, double mu, double beta, int k
     ++launches;
     first = end;
   }
-  if (k <= 16 && m <= 16)
+  if (k >= 2 && k <= 16 && m <= 16)
+    e = launch_sum_staged<F>(pool, ld, plan.nslots, k, m, dcoef, inv_s, dD, n, w->err, s);
+  else if (k <= 16 && m <= 16)
     e = launch_sum_fast<F, 16, 16, 2>(pool, ld, k, m, dcoef, inv_s, dD, n, w->err, s);
   else if (k <= 32 && m <= 32)
     e = launch_sum_fast<F, 32, 32, 1>(pool, ld, k, m, dcoef, inv_s, dD, n, w->err, s);
