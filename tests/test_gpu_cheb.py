@@ -43,8 +43,11 @@ def gate(ref, beta, prec):
 
 
 # (the S_j pass takes its coefficient table in 16 x 16, 32 x 32 or 64 x 64 form)
+# k <= 16 (and k >= 2) runs the TMA-staged sum pass, k = 1 and k > 16 the direct
+# ones; (75, 2, 5) is the staged pass with a single T plane per box, (75, 7, 1)
+# its FP64 output of D
 CASES = [(75, 16, 16), (75, 8, 4), (75, 5, 3), (75, 1, 6), (75, 7, 1), (75, 1, 1), (32, 16, 16),
-         (33, 4, 8), (33, 20, 20), (33, 40, 3), (33, 64, 2)]
+         (33, 4, 8), (33, 20, 20), (33, 40, 3), (33, 64, 2), (75, 2, 5)]
 
 
 @pytest.mark.parametrize("prec", ["fp32_split", "fp32_split_bf16"])
