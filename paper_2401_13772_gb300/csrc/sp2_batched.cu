@@ -506,7 +506,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         __syncwarp();
       }
-      double tr = 0.0, fr = 0.0;
+      // partial traces of this iteration: the FP32 sum of each 32-column chunk
+      // (the same chunks in every launch configuration) is added exactly on the
+      // 2^-40 grid in 64-bit integers, converted to FP64 once per iteration (FP64
+      // adds per tile held up the epilogue; the exact sums keep the traces, and
+      // with them the branch decisions, independent of the configuration)
+      long long tfix = 0, ffix = 0;
       if (epi) {
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const uint16_t* xs0 = prm.sl[src][0];
@@ -530,20 +535,28 @@ __global__ void __launch_bounds__(THREADS, 1)
               const int cofs = half * Cfg::COLS_PER_WARP + ch * 32;  // column in the tile
               const int c0 = J * BN + cofs;
               float trf = 0.0f, frf = 0.0f;
+              // X at the mirror (for 2X - X^2) does not depend on the products:
+              // load it before the tensor-memory reads (packed slice0 | slice1
+              // << 16; coalesced across the warp's rows). Two slices: both
+              // 16-column halves at once (one round of load latency per chunk)
+              uint32_t mm01[2][16], mm2[2][16];
+              auto load_mirror = [&](int hh) {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                  const size_t mi = (size_t)(in.row0 + c0 + hh * 16 + jj) * P + r;
+                  mm01[hh][jj] = (uint32_t)xs0[mi] | ((uint32_t)xs1[mi] << 16);
+                  mm2[hh][jj] = NS == 3 ? (uint32_t)xs2[mi] : 0u;
+                }
+              };
+              if (bit && NS == 2) {
+                load_mirror(0);
+                load_mirror(1);
+              }
 #pragma unroll
               for (int hh = 0; hh < 2; ++hh) {
-                // X at the mirror (for 2X - X^2) does not depend on the
-                // products: load it before the tensor-memory reads (packed
-                // slice0 | slice1 << 16; coalesced across the warp's rows)
-                uint32_t m01[16], m2[16];
-                if (bit) {
-#pragma unroll
-                  for (int jj = 0; jj < 16; ++jj) {
-                    const size_t mi = (size_t)(in.row0 + c0 + hh * 16 + jj) * P + r;
-                    m01[jj] = (uint32_t)xs0[mi] | ((uint32_t)xs1[mi] << 16);
-                    m2[jj] = NS == 3 ? (uint32_t)xs2[mi] : 0u;
-                  }
-                }
+                if (bit && NS == 3) load_mirror(hh);
+                const uint32_t* m01 = mm01[hh];
+                const uint32_t* m2 = mm2[hh];
                 uint32_t u0[16], u1[16];
                 tmem_ld16(tmem + lane_base + ACC_COLS * tb + cofs + hh * 16, u0);
                 tmem_ld16(tmem + lane_base + ACC_COLS * tb + BN + cofs + hh * 16, u1);
@@ -593,8 +606,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 __syncwarp();
               }
-              tr += (double)trf;
-              fr += (double)frf;
+              tfix += fixed40(trf);
+              ffix += fixed40(frf);
             }
           }
           tc_fence_before();
@@ -603,6 +616,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         fence_async_global();  // this iteration's slices feed the next TMA reads
       }
+      double tr = (double)tfix * 9.094947017729282e-13, fr = (double)ffix * 9.094947017729282e-13;  // 2^-40
       block_sum2(tr, fr, sh.red);  // all threads of the CTA meet here
       if (gsz > 1) {
         if (threadIdx.x == 0) xch_put(sh, xk & 1, grank, gsz, tr, fr, *err ? 1.0 : 0.0);

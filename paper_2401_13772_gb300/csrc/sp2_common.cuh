@@ -92,6 +92,27 @@ __device__ __forceinline__ double warp_max(double v) {
 
 // Block-wide sum of two doubles in a fixed order; result valid in thread 0.
 // `scratch` holds 2 * (blockDim.x / 32) doubles.
+// Compensated FP32 sum (Kahan): s - c carries the running total. The epilogues
+// use it for their partial traces instead of FP64 adds, which are slow on this
+// part (a few FP64 operations per clock and SM).
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// v (|v| < 2^7) on the fixed-point grid 2^-40, as an integer: v 2^16 is split
+// exactly into its integer part a and the rest, the rest is rounded at 2^-24 of
+// the unit (so v at 2^-40), all in FP32 and 32-bit conversions. Sums of these
+// integers are exact and do not depend on their order.
+__host__ __device__ __forceinline__ long long fixed40(float v) {
+  const float x = v * 65536.0f;     // exact
+  const float a = rintf(x);         // |a| < 2^23: exact in FP32 and int32
+  const float b = rintf((x - a) * 16777216.0f);  // x - a is exact; |b| <= 2^23
+  return (long long)(int)a * 16777216LL + (long long)(int)b;
+}
+
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* scratch) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   a = warp_sum(a);

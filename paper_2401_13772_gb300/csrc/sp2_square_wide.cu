@@ -92,14 +92,6 @@ struct WideCtx {
   int ld, T, bit, want_fp64, df, first_tile, tile_step;
 };
 
-// Compensated FP32 sum (Kahan): s + (-c) carries the running total.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
 // Epilogue of tile j of this CTA for one drain warp: its 32 rows (lanes) and
 // 64 columns of S = X*X, read from tensor memory at s_addr in 8-column pieces.
 // X' = S or 2X - S (the branch of §IV.A, decided before the product), its
