@@ -574,8 +574,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                   if (r <= c) {
                     uint16_t a, b, c2;
                     split_value_f<F>(x, a, b, c2);
-                    // (r, c) goes through the staging planes; its mirror
-                    // (c, r) is already contiguous across the warp's lanes
+                    // (r, c) goes through the staging planes (two slices: the
+                    // mirror (c, r) too, both written as 16-byte vectors below)
                     epA[lane * 17 + jj] = (uint32_t)a | ((uint32_t)b << 16);
                     if (NS == 3) epB[lane * 18 + jj] = c2;
                     if (r == c) {
@@ -583,25 +583,91 @@ __global__ void __launch_bounds__(THREADS, 1)
                       frf += x * x;
                     } else {
                       frf += 2.0f * x * x;
-                      const size_t mi = (size_t)(in.row0 + c) * P + r;
-                      o0[mi] = a;
-                      o1[mi] = b;
-                      if (NS == 3) o2[mi] = c2;
+                      if (NS == 3) {  // contiguous across the warp's lanes
+                        const size_t mi = (size_t)(in.row0 + c) * P + r;
+                        o0[mi] = a;
+                        o1[mi] = b;
+                        o2[mi] = c2;
+                      }
                     }
                   }
                 }
-                // 16 columns x 32 rows back out, two rows per store instruction
                 __syncwarp();
-                const int cc = c0 + hh * 16 + (lane & 15);
+                if (NS == 2) {
+                  // 32 rows x 16 columns of (hi | lo << 16) are staged: each lane
+                  // writes runs of 8 values of one slice as 16-byte vectors (2-byte
+                  // stores made the epilogue store-bound). Pitch and row offsets
+                  // are multiples of 128, so every run is 16-byte aligned; a run
+                  // that crosses the diagonal is written element by element.
+                  const int cb = c0 + hh * 16;
+                  auto pack = [](const uint32_t* w, bool hi) {
+                    uint4 v;
+                    uint32_t* pv = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                      pv[t] = hi ? ((w[2 * t] >> 16) | (w[2 * t + 1] & 0xffff0000u))
+                                 : ((w[2 * t] & 0xffffu) | (w[2 * t + 1] << 16));
+                    return v;
+                  };
+#pragma unroll
+                  for (int q = 0; q < 2; ++q) {  // (r, c): row i, columns cb + 8 g ..
+                    const int task = lane + 32 * q;
+                    const int i = task >> 1, g = task & 1;
+                    const int rr = rb + i, cs = cb + 8 * g;
+                    if (rr <= cs + 7) {
+                      uint32_t w[8];
+#pragma unroll
+                      for (int t = 0; t < 8; ++t) w[t] = epA[i * 17 + 8 * g + t];
+                      const size_t dd = (size_t)(in.row0 + rr) * P + cs;
+                      if (rr <= cs) {
+                        *reinterpret_cast<uint4*>(o0 + dd) = pack(w, false);
+                        *reinterpret_cast<uint4*>(o1 + dd) = pack(w, true);
+                      } else {
+#pragma unroll
+                        for (int t = 0; t < 8; ++t)
+                          if (rr <= cs + t) {
+                            o0[dd + t] = (uint16_t)(w[t] & 0xffffu);
+                            o1[dd + t] = (uint16_t)(w[t] >> 16);
+                          }
+                      }
+                    }
+                  }
+#pragma unroll
+                  for (int q = 0; q < 2; ++q) {  // mirror (c, r): column cb + j, rows rb + 8 g ..
+                    const int task = lane + 32 * q;
+                    const int j = task >> 2, g = task & 3;
+                    const int cc = cb + j, r0 = rb + 8 * g;
+                    if (r0 < cc) {
+                      uint32_t w[8];
+#pragma unroll
+                      for (int t = 0; t < 8; ++t) w[t] = epA[(8 * g + t) * 17 + j];
+                      const size_t mi = (size_t)(in.row0 + cc) * P + r0;
+                      if (r0 + 7 < cc) {
+                        *reinterpret_cast<uint4*>(o0 + mi) = pack(w, false);
+                        *reinterpret_cast<uint4*>(o1 + mi) = pack(w, true);
+                      } else {
+#pragma unroll
+                        for (int t = 0; t < 8; ++t)
+                          if (r0 + t < cc) {
+                            o0[mi + t] = (uint16_t)(w[t] & 0xffffu);
+                            o1[mi + t] = (uint16_t)(w[t] >> 16);
+                          }
+                      }
+                    }
+                  }
+                } else {
+                  // 16 columns x 32 rows back out, two rows per store instruction
+                  const int cc = c0 + hh * 16 + (lane & 15);
 #pragma unroll 4
-                for (int it = 0; it < 16; ++it) {
-                  const int i = 2 * it + (lane >> 4);
-                  if (rb + i <= cc) {
-                    const uint32_t v = epA[i * 17 + (lane & 15)];
-                    const size_t dd = (size_t)(in.row0 + rb + i) * P + cc;
-                    o0[dd] = (uint16_t)(v & 0xffffu);
-                    o1[dd] = (uint16_t)(v >> 16);
-                    if (NS == 3) o2[dd] = epB[i * 18 + (lane & 15)];
+                  for (int it = 0; it < 16; ++it) {
+                    const int i = 2 * it + (lane >> 4);
+                    if (rb + i <= cc) {
+                      const uint32_t v = epA[i * 17 + (lane & 15)];
+                      const size_t dd = (size_t)(in.row0 + rb + i) * P + cc;
+                      o0[dd] = (uint16_t)(v & 0xffffu);
+                      o1[dd] = (uint16_t)(v >> 16);
+                      if (NS == 3) o2[dd] = epB[i * 18 + (lane & 15)];
+                    }
                   }
                 }
                 __syncwarp();
