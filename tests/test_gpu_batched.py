@@ -183,15 +183,19 @@ def test_batched_launch_configs_match_oracle(pkg, mixed_batch, cfg):
 
 
 def test_batched_configs_agree_and_report_cycles(pkg, mixed_batch):
+    """Every launch configuration gives the same D bit for bit and the same
+    iteration counts: each element's products are the same tensor-core
+    operations in every tile width and cluster size, and the partial traces are
+    summed exactly (fixed point, 2^-40) whatever the grouping of tiles, so every
+    branch and stop decision is the same."""
     mats, noccs, refs, gates = mixed_batch
     base, it0, st0, cyc0 = run_cfg(pkg, mats, noccs, (128, 1, 1), cycles=True)
     assert (cyc0 > 0).all()
-    for cfg in [(64, 2, 1), (128, 4, 1)]:
+    for cfg in [(64, 2, 1), (128, 4, 1), (128, 2, 2), (64, 1, 1)]:
         outs, it, st, cyc = run_cfg(pkg, mats, noccs, cfg, cycles=True)
         assert (cyc > 0).all()
-        assert np.abs(it.astype(int) - it0.astype(int)).max() <= 2
-        for D0, D, g in zip(base, outs, gates):
-            assert float(np.abs(D - D0).max()) <= 2 * g
+        assert np.array_equal(it, it0), cfg
+        assert all(np.array_equal(D0, D) for D0, D in zip(base, outs)), cfg
     # the same configuration twice: bit-identical
     again, it1, st1 = run_cfg(pkg, mats, noccs, (128, 4, 1))[:3]
     outs, it2, st2 = run_cfg(pkg, mats, noccs, (128, 4, 1))[:3]
