@@ -574,8 +574,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                   if (r <= c) {
                     uint16_t a, b, c2;
                     split_value_f<F>(x, a, b, c2);
-                    // (r, c) goes through the staging planes (two slices: the
-                    // mirror (c, r) too, both written as 16-byte vectors below)
+                    // (r, c) and its mirror (c, r) go through the staging planes
+                    // and are written as 16-byte vectors below
                     epA[lane * 17 + jj] = (uint32_t)a | ((uint32_t)b << 16);
                     if (NS == 3) epB[lane * 18 + jj] = c2;
                     if (r == c) {
@@ -583,22 +583,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                       frf += x * x;
                     } else {
                       frf += 2.0f * x * x;
-                      if (NS == 3) {  // contiguous across the warp's lanes
-                        const size_t mi = (size_t)(in.row0 + c) * P + r;
-                        o0[mi] = a;
-                        o1[mi] = b;
-                        o2[mi] = c2;
-                      }
                     }
                   }
                 }
                 __syncwarp();
-                if (NS == 2) {
-                  // 32 rows x 16 columns of (hi | lo << 16) are staged: each lane
-                  // writes runs of 8 values of one slice as 16-byte vectors (2-byte
-                  // stores made the epilogue store-bound). Pitch and row offsets
-                  // are multiples of 128, so every run is 16-byte aligned; a run
-                  // that crosses the diagonal is written element by element.
+                {
+                  // 32 rows x 16 columns of (slice0 | slice1 << 16) are staged (and
+                  // slice 2 beside them): each lane writes runs of 8 values of one
+                  // slice as 16-byte vectors (2-byte stores made the epilogue
+                  // store-bound). Pitch and row offsets are multiples of 128, so
+                  // every run is 16-byte aligned; a run that crosses the diagonal
+                  // is written element by element.
                   const int cb = c0 + hh * 16;
                   auto pack = [](const uint32_t* w, bool hi) {
                     uint4 v;
@@ -607,6 +602,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int t = 0; t < 4; ++t)
                       pv[t] = hi ? ((w[2 * t] >> 16) | (w[2 * t + 1] & 0xffff0000u))
                                  : ((w[2 * t] & 0xffffu) | (w[2 * t + 1] << 16));
+                    return v;
+                  };
+                  // 8 slice-2 values at p, p + stride, ..., packed for one store
+                  auto pack16 = [](const uint16_t* p, int stride) {
+                    uint4 v;
+                    uint32_t* pv = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                      pv[t] = (uint32_t)p[2 * t * stride] | ((uint32_t)p[(2 * t + 1) * stride] << 16);
                     return v;
                   };
 #pragma unroll
@@ -622,12 +626,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                       if (rr <= cs) {
                         *reinterpret_cast<uint4*>(o0 + dd) = pack(w, false);
                         *reinterpret_cast<uint4*>(o1 + dd) = pack(w, true);
+                        if (NS == 3)
+                          *reinterpret_cast<uint4*>(o2 + dd) = pack16(epB + i * 18 + 8 * g, 1);
                       } else {
 #pragma unroll
                         for (int t = 0; t < 8; ++t)
                           if (rr <= cs + t) {
                             o0[dd + t] = (uint16_t)(w[t] & 0xffffu);
                             o1[dd + t] = (uint16_t)(w[t] >> 16);
+                            if (NS == 3) o2[dd + t] = epB[i * 18 + 8 * g + t];
                           }
                       }
                     }
@@ -645,28 +652,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                       if (r0 + 7 < cc) {
                         *reinterpret_cast<uint4*>(o0 + mi) = pack(w, false);
                         *reinterpret_cast<uint4*>(o1 + mi) = pack(w, true);
+                        if (NS == 3)
+                          *reinterpret_cast<uint4*>(o2 + mi) = pack16(epB + (8 * g) * 18 + j, 18);
                       } else {
 #pragma unroll
                         for (int t = 0; t < 8; ++t)
                           if (r0 + t < cc) {
                             o0[mi + t] = (uint16_t)(w[t] & 0xffffu);
                             o1[mi + t] = (uint16_t)(w[t] >> 16);
+                            if (NS == 3) o2[mi + t] = epB[(8 * g + t) * 18 + j];
                           }
                       }
-                    }
-                  }
-                } else {
-                  // 16 columns x 32 rows back out, two rows per store instruction
-                  const int cc = c0 + hh * 16 + (lane & 15);
-#pragma unroll 4
-                  for (int it = 0; it < 16; ++it) {
-                    const int i = 2 * it + (lane >> 4);
-                    if (rb + i <= cc) {
-                      const uint32_t v = epA[i * 17 + (lane & 15)];
-                      const size_t dd = (size_t)(in.row0 + rb + i) * P + cc;
-                      o0[dd] = (uint16_t)(v & 0xffffu);
-                      o1[dd] = (uint16_t)(v >> 16);
-                      if (NS == 3) o2[dd] = epB[i * 18 + (lane & 15)];
                     }
                   }
                 }
